@@ -1,0 +1,169 @@
+"""FP64 CPU oracle for the SNeRG deferred volume render.
+
+TEST INFRASTRUCTURE ONLY: this package may be imported by `tests/`, by
+`__graft_entry__.smoke()` and by the CPU-baseline leg of `bench.py`, and by nothing in
+the product path. It shares no code with the CUDA renderer; the only thing both sides
+consume is the seeded input generator (`paper_2103_14645_gb300.synth`), which holds none
+of the method's arithmetic, and this wrapper reads scenes from it by attribute only.
+
+The arithmetic lives in `snerg_oracle.c` (plain C, FP64 colour arithmetic, binary32
+integer decisions in a fixed operation order, `-ffp-contract=off`); every function there
+cites the paper passage it follows (Sec. 4.2 Eqs. 2, 5-7; Sec. 5.1-5.2; App. A; Sec. 5.5).
+
+Parity pins (tests/test_oracle_pins.py) tie it to closed forms, invariants, library
+routines and brute force on tiny grids. No function here is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "snerg_oracle.c")
+_SO = os.path.join(_HERE, "libsnerg_oracle.so")
+_LIB = None
+
+NPARAM = 883
+MLP_IN = 34
+
+
+def build_oracle(verbose: bool = False) -> str:
+    """Compile the oracle with gcc. -ffp-contract=off keeps every binary32 operation a
+    single rounding (aarch64 GCC would otherwise contract a*b+c to fma)."""
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True, capture_output=not verbose)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            build_oracle()
+        lib = ctypes.CDLL(_SO)
+        P, i32, i64, f32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+        common = [i32, i32, P, f32, f64, P, P, P, P, i64, P, P, i32, P, i64]
+        lib.oracle_render_rays.argtypes = common + [P, P, P, P, i32]
+        lib.oracle_render_rays.restype = ctypes.c_int
+        lib.oracle_backward_rays.argtypes = common + [P, P, P]
+        lib.oracle_backward_rays.restype = ctypes.c_int
+        lib.oracle_mlp_eval.argtypes = [P, P, i64, P]
+        lib.oracle_mlp_eval.restype = None
+        lib.oracle_mlp_input.argtypes = [P, P, P, P]
+        lib.oracle_mlp_input.restype = None
+        lib.oracle_ray.argtypes = [i32, f32, P, P, i32, i32, P]
+        lib.oracle_ray.restype = ctypes.c_int
+        _LIB = lib
+    return _LIB
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def cameras_f32(cams) -> np.ndarray:
+    """Camera records -> float32 [n][16] = c2w (12), fx, fy, cx, cy."""
+    out = np.zeros((len(cams), 16), np.float32)
+    for i, c in enumerate(cams):
+        out[i, :12] = np.asarray(c["c2w"], np.float32).reshape(-1)
+        out[i, 12:] = [c["fx"], c["fy"], c["cx"], c["cy"]]
+    return out
+
+
+def _scene_args(scene, val, mlp, cams):
+    bmin = np.asarray(scene.bmin, np.float32)
+    bg = np.asarray(scene.bg, np.float64)
+    ind = np.ascontiguousarray(scene.ind, np.int32)
+    atlas = np.ascontiguousarray(scene.atlas, np.uint8)
+    if val is not None:
+        val = np.ascontiguousarray(val, np.float64)
+        assert val.size == atlas.size
+    w = np.ascontiguousarray(scene.mlp if mlp is None else mlp, np.float64)
+    assert w.size == NPARAM
+    cf = cameras_f32(scene.cameras if cams is None else cams)
+    keep = (bmin, bg, ind, atlas, val, w, cf)
+    args = [int(scene.N), int(scene.B), _p(bmin), float(scene.extent), float(scene.sigma_max), _p(bg),
+            _p(ind), _p(atlas), _p(val), int(atlas.shape[0]), _p(w), _p(cf), int(cf.shape[0])]
+    return args, keep
+
+
+def render_rays(scene, pix, mlp=None, val=None, cams=None, trace_cap: int = 0):
+    """Render rays pix[n][3] = (camera, x, y). Returns a dict with
+    rgb [n,3] f64, aux [n,8] f64 (C_d, V, acc), counts [n,2] int32 (steps, active) and,
+    when trace_cap > 0, trace [n,trace_cap] uint64 (visited voxel indices, 0-padded)."""
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 3)
+    n = pix.shape[0]
+    args, keep = _scene_args(scene, val, mlp, cams)
+    rgb = np.zeros((n, 3), np.float64)
+    aux = np.zeros((n, 8), np.float64)
+    counts = np.zeros((n, 2), np.int32)
+    trace = np.zeros((n, trace_cap), np.uint64) if trace_cap > 0 else None
+    st = _lib().oracle_render_rays(*args, _p(pix), n, _p(rgb), _p(aux), _p(counts), _p(trace), int(trace_cap))
+    if st:
+        raise OracleError(f"oracle_render_rays status {st}")
+    out = {"rgb": rgb, "aux": aux, "counts": counts}
+    if trace is not None:
+        out["trace"] = trace
+    return out
+
+
+def render_image(scene, cam_index: int = 0, mlp=None, val=None):
+    """Full image of one camera as [H, W, 3] f64 (plus aux/counts reshaped)."""
+    c = scene.cameras[cam_index]
+    W, H = int(c["W"]), int(c["H"])
+    y, x = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    pix = np.stack([np.full(W * H, cam_index), x.ravel(), y.ravel()], 1).astype(np.int32)
+    out = render_rays(scene, pix, mlp=mlp, val=val)
+    return {k: v.reshape(H, W, -1) for k, v in out.items()}
+
+
+def backward_rays(scene, pix, g_rgb, mlp=None, val=None, cams=None):
+    """Adjoint for upstream dL/dC g_rgb[n,3]. Returns (grad_val [nb,B,B,B,8] f64 with
+    channel 0 zero, grad_mlp [883] f64)."""
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 3)
+    g = np.ascontiguousarray(g_rgb, np.float64).reshape(-1, 3)
+    assert g.shape[0] == pix.shape[0]
+    args, keep = _scene_args(scene, val, mlp, cams)
+    grad = np.zeros(scene.atlas.shape, np.float64)
+    gmlp = np.zeros(NPARAM, np.float64)
+    st = _lib().oracle_backward_rays(*args, _p(pix), pix.shape[0], _p(g), _p(grad), _p(gmlp))
+    if st:
+        raise OracleError(f"oracle_backward_rays status {st}")
+    return grad, gmlp
+
+
+def mlp_eval(mlp, x):
+    """sigmoid(MLP(x)) for x[n,34] (FP64)."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, MLP_IN)
+    w = np.ascontiguousarray(mlp, np.float64)
+    out = np.zeros((x.shape[0], 3), np.float64)
+    _lib().oracle_mlp_eval(_p(w), _p(x), x.shape[0], _p(out))
+    return out
+
+
+def mlp_input(cd, v, d):
+    cd = np.ascontiguousarray(cd, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    d = np.ascontiguousarray(d, np.float32)
+    x = np.zeros(MLP_IN, np.float64)
+    _lib().oracle_mlp_input(_p(cd), _p(v), _p(d), _p(x))
+    return x
+
+
+def ray(scene, cam, px: int, py: int):
+    """(hit, o[3], d[3], t_start, t_end) of one pixel, in voxel units (binary32)."""
+    cf = cameras_f32([cam])[0]
+    bmin = np.asarray(scene.bmin, np.float32)
+    out = np.zeros(8, np.float32)
+    hit = _lib().oracle_ray(int(scene.N), float(scene.extent), _p(bmin), _p(cf), int(px), int(py), _p(out))
+    return bool(hit), out[0:3].copy(), out[3:6].copy(), float(out[6]), float(out[7])

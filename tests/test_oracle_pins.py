@@ -1,0 +1,387 @@
+"""Pins for the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these retypes the oracle: each checks a closed form (uniform slab, two-sample
+ray, early-exit count), an invariant (weights sum to 1 - T, slot permutation,
+zero-density blocks), a library routine (torch float64 linear layers, scipy trilinear
+interpolation) or a brute-force evaluation on a tiny grid. A plausible mistake in the
+oracle (dropped transmittance factor, wrong alpha sign, transposed weight, off-by-one
+in the sample lattice, wrong trilinear corner) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2103_14645_gb300 import synth
+from tests import helpers
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _pix(scene, cam=0):
+    return synth.all_pixels(scene.cameras[cam:cam + 1])
+
+
+# --------------------------------------------------------------------------------------
+# closed forms
+# --------------------------------------------------------------------------------------
+
+def test_empty_grid_returns_background():
+    """No occupied block: every ray returns the background exactly (Eq. 2 with no samples)."""
+    sc = synth.make_scene("tiny")
+    sc.ind[:] = -1
+    out = oracle.render_rays(sc, _pix(sc), trace_cap=4)
+    assert np.array_equal(out["rgb"], np.tile(np.asarray(sc.bg), (out["rgb"].shape[0], 1)))
+    assert (out["counts"] == 0).all()
+    assert (out["aux"] == 0).all()
+
+
+def test_uniform_slab_transmittance():
+    """Axis ray through M voxels of uniform density: T = exp(-sigma L), C_d = c (1 - T)."""
+    q = 200
+    col = np.array([100, 150, 200, 10, 20, 30, 40])
+    sc = helpers.slab_scene(z_range=(4, 6), q=q, color=col, sigma_max_vox=1.0)
+    out = oracle.render_rays(sc, np.array([[0, 0, 0]]), trace_cap=8)
+    sigma_delta = q / 255.0 * 1.0
+    T = math.exp(-2 * sigma_delta)
+    cd = col[:3] / 255.0 * (1 - T)
+    v = col[3:] / 255.0 * (1 - T)
+    np.testing.assert_allclose(out["aux"][0, :3], cd, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(out["aux"][0, 3:7], v, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(out["aux"][0, 7], 1 - T, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(out["rgb"][0], cd + T * np.asarray(sc.bg), rtol=0, atol=1e-14)
+    # the ray enters block row bz=1 (z in [4,8)) at u_z = 7.5: 4 samples there, 2 composited
+    assert out["counts"][0].tolist() == [4, 2]
+    N = sc.N
+    assert out["trace"][0, :2].tolist() == [(5 * N + 5) * N + 5, (4 * N + 5) * N + 5]
+
+
+def test_two_sample_ray_by_hand():
+    """Two voxels of different density along the ray: w1 = 1 - e^-a, w2 = e^-a (1 - e^-b)."""
+    col = np.array([255, 0, 51, 0, 0, 0, 255])
+    sc = helpers.slab_scene(z_range=(4, 6), per_voxel_q=(51, 204), color=col, sigma_max_vox=2.0)
+    out = oracle.render_rays(sc, np.array([[0, 0, 0]]))
+    a = 204 / 255.0 * 2.0    # voxel z=5 is met first (the ray travels towards -z)
+    b = 51 / 255.0 * 2.0
+    w1 = 1 - math.exp(-a)
+    w2 = math.exp(-a) * (1 - math.exp(-b))
+    T = math.exp(-a - b)
+    expect = np.array([w1 + w2, 0.0, 0.2 * (w1 + w2)]) + T * 1.0
+    np.testing.assert_allclose(out["rgb"][0], expect, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(out["aux"][0, 6], w1 + w2, rtol=0, atol=1e-14)
+
+
+def test_early_exit_after_crossing_sample():
+    """Opaque slab with sigma*delta = 1 per sample: marching stops after the first sample
+    where the optical depth exceeds ln(1000), i.e. after floor(ln 1000) + 1 = 7 samples."""
+    sc = helpers.slab_scene(z_range=(2, 14), q=255, sigma_max_vox=1.0)
+    out = oracle.render_rays(sc, np.array([[0, 0, 0]]), trace_cap=16)
+    n_active = math.floor(math.log(1000.0)) + 1
+    assert out["counts"][0, 1] == n_active
+    # block row bz=3 (z 12..15) is entered at u_z=15.5: 2 non-composited samples first
+    assert out["counts"][0, 0] == 2 + n_active
+    np.testing.assert_allclose(1 - out["aux"][0, 7], math.exp(-n_active), rtol=1e-12)
+
+
+def test_zero_weights_residual_is_half():
+    """W = 0, b = 0: sigmoid(0) = 1/2 is added only where a sample was composited."""
+    sc = synth.make_scene("tiny")
+    w = np.zeros(synth.MLP_NPARAM, np.float32)
+    out = oracle.render_rays(sc, _pix(sc), mlp=w)
+    act = out["counts"][:, 1] > 0
+    assert act.any() and (~act).any()
+    T = 1 - out["aux"][:, 7]
+    np.testing.assert_allclose(out["rgb"][act], out["aux"][act, :3] + 0.5 + T[act, None], atol=1e-14)
+    np.testing.assert_array_equal(out["rgb"][~act], np.ones(((~act).sum(), 3)))
+
+
+def test_saturated_bias_gives_diffuse_plus_background():
+    sc = synth.make_scene("tiny")
+    out = oracle.render_rays(sc, _pix(sc), mlp=helpers.silent_mlp())
+    T = 1 - out["aux"][:, 7]
+    np.testing.assert_allclose(out["rgb"], out["aux"][:, :3] + T[:, None] * 1.0, rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------------------------------------------
+# invariants
+# --------------------------------------------------------------------------------------
+
+def test_weights_sum_to_opacity():
+    """Sum_k w_k = 1 - T_final <= 1: with every block stored and every colour value 1,
+    C_d equals the opacity (corners in empty blocks would read 0)."""
+    sc0 = synth.make_scene("gauss64")
+    ind, atlas = helpers.dense_to_blocks(helpers.blocks_to_dense(sc0), sc0.B, keep_empty=True)
+    sc = synth.custom_scene(sc0.N, sc0.B, ind, atlas, sc0.sigma_max, sc0.mlp, sc0.cameras)
+    val = np.ones(sc.atlas.shape, np.float64)
+    out = oracle.render_rays(sc, _pix(sc), val=val)
+    acc = out["aux"][:, 7]
+    assert (acc >= 0).all() and (acc <= 1).all()
+    for c in range(7):
+        np.testing.assert_allclose(out["aux"][:, c], acc, rtol=0, atol=1e-12)
+    assert (out["counts"][:, 1] > 0).mean() > 0.3
+
+
+def test_colours_bounded_by_opacity():
+    sc = synth.make_scene("gauss64")
+    out = oracle.render_rays(sc, _pix(sc))
+    acc = out["aux"][:, 7]
+    assert (out["aux"][:, :7] <= acc[:, None] + 1e-12).all()
+    assert (out["aux"][:, :7] >= 0).all()
+
+
+def test_atlas_slot_permutation_invariance():
+    """The indirection grid is the only link from space to atlas slots (Sec. 5.1)."""
+    sc = synth.make_scene("tiny")
+    ref = oracle.render_rays(sc, _pix(sc), trace_cap=64)
+    perm = np.random.default_rng(3).permutation(sc.nb)
+    inv = np.argsort(perm)
+    sc2 = synth.custom_scene(sc.N, sc.B, np.where(sc.ind >= 0, inv[np.maximum(sc.ind, 0)], -1),
+                             sc.atlas[perm], sc.sigma_max, sc.mlp, sc.cameras)
+    out = oracle.render_rays(sc2, _pix(sc2), trace_cap=64)
+    for k in ("rgb", "aux", "counts", "trace"):
+        assert np.array_equal(ref[k], out[k]), k
+
+
+def test_zero_density_blocks_equal_empty_blocks():
+    """Storing an all-zero block changes the step count only, never the image."""
+    sc = synth.make_scene("tiny")
+    dense = helpers.blocks_to_dense(sc)
+    ind_all, atlas_all = helpers.dense_to_blocks(dense, sc.B, keep_empty=True)
+    # stored-but-zero blocks must also have zero colour to match "empty reads 0"
+    sc_all = synth.custom_scene(sc.N, sc.B, ind_all, atlas_all, sc.sigma_max, sc.mlp, sc.cameras)
+    a = oracle.render_rays(sc, _pix(sc), trace_cap=64)
+    b = oracle.render_rays(sc_all, _pix(sc_all), trace_cap=64)
+    assert np.array_equal(a["rgb"], b["rgb"])
+    assert np.array_equal(a["trace"], b["trace"])
+    assert np.array_equal(a["counts"][:, 1], b["counts"][:, 1])
+    assert (b["counts"][:, 0] >= a["counts"][:, 0]).all() and (b["counts"][:, 0] > a["counts"][:, 0]).any()
+
+
+# --------------------------------------------------------------------------------------
+# library routines
+# --------------------------------------------------------------------------------------
+
+def _torch_mlp(w, x):
+    w = torch.as_tensor(np.asarray(w, np.float64))
+    x = torch.as_tensor(np.asarray(x, np.float64))
+    o = 0
+    W1 = w[o:o + 16 * 34].reshape(16, 34); o += 16 * 34
+    b1 = w[o:o + 16]; o += 16
+    W2 = w[o:o + 256].reshape(16, 16); o += 256
+    b2 = w[o:o + 16]; o += 16
+    W3 = w[o:o + 48].reshape(3, 16); o += 48
+    b3 = w[o:o + 3]
+    F = torch.nn.functional
+    h = F.relu(F.linear(x, W1, b1))
+    h = F.relu(F.linear(h, W2, b2))
+    return torch.sigmoid(F.linear(h, W3, b3)).numpy()
+
+
+def test_mlp_matches_torch_float64():
+    rng = np.random.default_rng(11)
+    w = rng.normal(size=synth.MLP_NPARAM)
+    x = rng.normal(size=(257, 34))
+    np.testing.assert_allclose(oracle.mlp_eval(w, x), _torch_mlp(w, x), rtol=0, atol=1e-14)
+
+
+def test_mlp_input_layout():
+    """Input = [C_d(3), V(4), d(3), sin(2^l d)(3), cos(2^l d)(3) for l = 0..3] (34)."""
+    rng = np.random.default_rng(12)
+    cd, v = rng.uniform(size=3), rng.uniform(size=4)
+    d = rng.normal(size=3).astype(np.float32)
+    d /= np.linalg.norm(d)
+    x = oracle.mlp_input(cd, v, d)
+    dd = d.astype(np.float64)
+    ref = [cd, v, dd]
+    for l in range(4):
+        ref += [np.sin(2.0 ** l * dd), np.cos(2.0 ** l * dd)]
+    np.testing.assert_allclose(x, np.concatenate(ref), rtol=0, atol=1e-15)
+
+
+def _brute_force_ray(scene, dense, mlp, cam, px, py):
+    """Definition of the march evaluated by library routines on a dense grid:
+    trilinear by scipy.ndimage.map_coordinates (order 1, clamp-to-edge), transmittance
+    by a running product, MLP by torch float64 linear layers."""
+    from scipy.ndimage import map_coordinates
+    N, B = scene.N, scene.B
+    hit, o, d, ts, te = oracle.ray(scene, cam, px, py)
+    dens = dense[..., 0].astype(np.float64)
+    chans = [dense[..., c].astype(np.float64) / 255.0 for c in range(1, 8)]
+    occ = scene.ind >= 0
+    delta = scene.extent / N
+    T, feat, steps, visited, tau = 1.0, np.zeros(7), 0, [], 0.0
+    k = 0
+    while hit:
+        tk = np.float32(ts) + (np.float32(k) + np.float32(0.5))
+        k += 1
+        if not tk < np.float32(te):
+            break
+        u = np.asarray(o, np.float32) + np.float32(tk) * np.asarray(d, np.float32)
+        j = np.clip(np.floor(u).astype(np.int64), 0, N - 1)
+        if not occ[j[2] // B, j[1] // B, j[0] // B]:
+            continue
+        steps += 1
+        if dense[j[2], j[1], j[0], 0] == 0:
+            continue
+        visited.append(int((j[2] * N + j[1]) * N + j[0]))
+        coord = (np.asarray(u[::-1], np.float64) - 0.5).reshape(3, 1)
+        s = map_coordinates(dens, coord, order=1, mode="nearest")[0]
+        sd = s / 255.0 * scene.sigma_max * delta
+        w = T * (1 - math.exp(-sd))
+        for c in range(7):
+            feat[c] += w * map_coordinates(chans[c], coord, order=1, mode="nearest")[0]
+        T *= math.exp(-sd)
+        tau += sd
+        if tau > math.log(1000.0):
+            break
+    rgb = np.asarray(scene.bg) * T
+    if visited:
+        dd = np.asarray(d, np.float64)
+        pe = [feat[:3], feat[3:], dd]
+        for l in range(4):
+            pe += [np.sin(2.0 ** l * dd), np.cos(2.0 ** l * dd)]
+        rgb = rgb + feat[:3] + _torch_mlp(mlp, np.concatenate(pe)[None])[0]
+    return rgb, feat, steps, visited
+
+
+@pytest.mark.parametrize("name", ["tiny", "gauss64"])
+def test_brute_force_dense_grid(name):
+    sc = synth.make_scene(name)
+    dense = helpers.blocks_to_dense(sc)
+    rng = np.random.default_rng(5)
+    W, H = int(sc.cameras[0]["W"]), int(sc.cameras[0]["H"])
+    pix = np.stack([np.zeros(60, int), rng.integers(0, W, 60), rng.integers(0, H, 60)], 1)
+    out = oracle.render_rays(sc, pix, trace_cap=256)
+    n_active_rays = 0
+    for i, (c, x, y) in enumerate(pix):
+        rgb, feat, steps, visited = _brute_force_ray(sc, dense, sc.mlp, sc.cameras[c], x, y)
+        np.testing.assert_allclose(out["rgb"][i], rgb, rtol=0, atol=1e-10)
+        np.testing.assert_allclose(out["aux"][i, :7], feat, rtol=0, atol=1e-10)
+        assert out["counts"][i, 0] == steps
+        assert out["counts"][i, 1] == len(visited)
+        assert out["trace"][i, :len(visited)].tolist() == visited
+        n_active_rays += bool(visited)
+    assert n_active_rays >= 10
+
+
+# --------------------------------------------------------------------------------------
+# ray geometry (pinhole, Sec. 4.1 r(t) = o + t d)
+# --------------------------------------------------------------------------------------
+
+def test_ray_geometry_pinhole():
+    sc = synth.make_scene("gauss64")
+    rng = np.random.default_rng(9)
+    cams = synth.orbit_cameras(rng, [(65, 47)] * 6, synth.CAM_RADIUS)
+    s = sc.N / sc.extent
+    for cam in cams:
+        c2w = np.asarray(cam["c2w"], np.float64).reshape(3, 4)
+        for _ in range(20):
+            px, py = int(rng.integers(0, 65)), int(rng.integers(0, 47))
+            hit, o, d, ts, te = oracle.ray(sc, cam, px, py)
+            xs = (px + 0.5 - cam["cx"]) / cam["fx"]
+            ys = (py + 0.5 - cam["cy"]) / cam["fy"]
+            assert abs(np.linalg.norm(d.astype(np.float64)) - 1) < 1e-6
+            ang = math.acos(float(np.clip(-(d.astype(np.float64) @ c2w[:, 2]), -1, 1)))
+            assert abs(ang - math.atan(math.hypot(xs, ys))) < 1e-5
+            np.testing.assert_allclose(o, (c2w[:, 3] - np.asarray(sc.bmin)) * s, atol=1e-4)
+            if hit:
+                for t, name in ((ts, "start"), (te, "end")):
+                    p = o.astype(np.float64) + t * d.astype(np.float64)
+                    assert (p > -1e-3).all() and (p < sc.N + 1e-3).all(), name
+                pe = o.astype(np.float64) + te * d.astype(np.float64)
+                on_face = np.minimum(np.abs(pe), np.abs(pe - sc.N)).min()
+                assert on_face < 1e-3
+
+
+def test_principal_ray_hits_look_at_target():
+    """Odd image width/height: the centre pixel looks straight at the target (origin)."""
+    sc = synth.make_scene("gauss64")
+    cam = synth.look_at_camera((1.3, -1.1, 0.9), (0.0, 0.0, 0.0), 65, 33, 39.0)
+    hit, o, d, ts, te = oracle.ray(sc, cam, 32, 16)
+    centre = (np.zeros(3) - np.asarray(sc.bmin)) * sc.N / sc.extent
+    rel = centre - o.astype(np.float64)
+    dist = np.linalg.norm(rel - (rel @ d) * d.astype(np.float64))
+    assert dist < 1e-3
+    # image y grows downwards: the top row looks further up (+z) than the bottom row
+    _, _, d_top, _, _ = oracle.ray(sc, cam, 32, 0)
+    _, _, d_bot, _, _ = oracle.ray(sc, cam, 32, 32)
+    assert d_top[2] > d[2] > d_bot[2]
+
+
+# --------------------------------------------------------------------------------------
+# gradient (adjoint of the render w.r.t. colour/feature values and MLP weights)
+# --------------------------------------------------------------------------------------
+
+def _loss(sc, pix, target, val=None, mlp=None):
+    out = oracle.render_rays(sc, pix, val=val, mlp=mlp)
+    return 0.5 * ((out["rgb"] - target) ** 2).sum(), out
+
+
+def test_gradient_matches_central_differences():
+    sc = synth.make_scene("tiny")
+    rng = np.random.default_rng(21)
+    pix = _pix(sc)
+    target = rng.uniform(size=(pix.shape[0], 3))
+    val = sc.atlas.astype(np.float64) / 255.0
+    mlp = sc.mlp.astype(np.float64)
+    L0, out = _loss(sc, pix, target, val, mlp)
+    gval, gmlp = oracle.backward_rays(sc, pix, out["rgb"] - target, val=val, mlp=mlp)
+    assert (gval[..., 0] == 0).all()
+    h = 1e-6
+    flat = gval.reshape(-1)
+    nz = np.nonzero(np.abs(flat) > 1e-6)[0]
+    nz = nz[nz % 8 != 0]
+    picks = list(rng.choice(nz, 24, replace=False)) + list(rng.choice(flat.size, 8, replace=False))
+    for idx in picks:
+        vp, vm = val.copy().reshape(-1), val.copy().reshape(-1)
+        vp[idx] += h
+        vm[idx] -= h
+        fd = (_loss(sc, pix, target, vp.reshape(val.shape), mlp)[0] -
+              _loss(sc, pix, target, vm.reshape(val.shape), mlp)[0]) / (2 * h)
+        if idx % 8 == 0:
+            continue      # density is frozen: the oracle reports no gradient for it
+        assert abs(fd - flat[idx]) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, flat[idx])
+    for p in rng.choice(synth.MLP_NPARAM, 32, replace=False):
+        mp, mm = mlp.copy(), mlp.copy()
+        mp[p] += h
+        mm[p] -= h
+        fd = (_loss(sc, pix, target, val, mp)[0] - _loss(sc, pix, target, val, mm)[0]) / (2 * h)
+        assert abs(fd - gmlp[p]) <= 1e-6 * max(1.0, abs(fd)), (p, fd, gmlp[p])
+
+
+def test_gradient_sum_equals_opacity_when_linear():
+    """Silent MLP and every block stored: C = C_d + T bg is linear in the colours, and the
+    red-channel gradient summed over all voxels equals the summed opacity (the trilinear
+    weights of each sample sum to one, and the composite weights to 1 - T)."""
+    sc = synth.make_scene("tiny")
+    dense = helpers.blocks_to_dense(sc)
+    ind, atlas = helpers.dense_to_blocks(dense, sc.B, keep_empty=True)
+    sc2 = synth.custom_scene(sc.N, sc.B, ind, atlas, sc.sigma_max, helpers.silent_mlp(), sc.cameras)
+    pix = _pix(sc2)
+    out = oracle.render_rays(sc2, pix)
+    g = np.zeros((pix.shape[0], 3))
+    g[:, 0] = 1.0
+    gval, gmlp = oracle.backward_rays(sc2, pix, g)
+    np.testing.assert_allclose(gval[..., 1].sum(), out["aux"][:, 7].sum(), rtol=1e-12)
+    assert np.abs(gval[..., 2:]).max() == 0.0
+    assert np.abs(gmlp).max() == 0.0      # sigmoid'(-1e4) underflows to exactly 0
+
+
+# --------------------------------------------------------------------------------------
+# constants the paper prints
+# --------------------------------------------------------------------------------------
+
+def test_paper_constants():
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        g = json.load(f)
+    assert synth.TAU_ALPHA == g["tau_alpha"]["value"]
+    assert synth.MLP_HID == g["view_mlp_width"]["value"]
+    assert len([s for s in synth.MLP_SIZES if len(s) == 2]) - 1 == g["view_mlp_hidden_layers"]["value"]
+    # 8 channels of 8 bits at 8 trilinear corners = the 64 bytes per sample of App. A
+    assert 8 * 8 == g["bytes_per_trilinear_sample"]["value"]
+    assert synth.make_scene("shell1024").B == g["macroblock_edge"]["value"]
+    assert synth.MLP_IN - 7 == 3 + 3 * 2 * 4    # direction + 4 octaves of sin/cos
