@@ -1,0 +1,371 @@
+"""Benchmark of the SNeRG deferred volume render on one node.
+
+Default (no flags): N=1. Workload of the headline number: the 1024^3 grid (32^3
+macroblocks, ~5% occupied, thin shells on seeded closed surfaces) rendered as one
+800x800 view at 39 degrees FOV (the paper's Synthetic 360 set-up, App. B). A step is one
+forward render of that view (ray generation, block-skipping march, density probe,
+trilinear fetch, compositing, early exit, per-pixel MLP, store). The same JSON line also
+carries the batched multi-camera render (64 cameras of mixed resolutions in one
+persistent graph launch, vs one launch per camera) and the forward+backward of 65,536
+rays on the 512^3 grid, each timed the same way.
+
+Timing: CUDA events on the launching stream around each step, L2 flushed (256 MiB
+write) before every timed step, W untimed warm-up steps, barrier + synchronize around
+the timed region, max over ranks. Under torchrun (N>1) each rank renders its own seeded
+view of the same grid (weak scaling, no data-path collective).
+
+--impl reference: the FP64 CPU oracle timed on this machine's host cores on the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s & 800² frames/s, batched vs plain; fwd+bwd Mrays/s; % HBM roofline"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "render_image_shell1024.md")
+CSRC = os.path.join(ROOT, "paper_2103_14645_gb300", "csrc")
+
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            txt = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_digest") != kernel_source_digest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# -------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# -------------------------------------------------------------------------------------
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2103_14645_gb300 import synth
+    sc = synth.make_scene("shell1024")
+    pix_all = synth.all_pixels(sc.cameras)
+    # a bounded sample per step: a seeded quarter of the view's rays
+    rng = np.random.default_rng(0)
+    n = pix_all.shape[0] // 4
+    samples = [pix_all[rng.choice(pix_all.shape[0], n, replace=False)] for _ in range(4)]
+    oracle.render_rays(sc, samples[0][:1000])
+    for i in range(args.warmup):
+        oracle.render_rays(sc, samples[i % 4])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.render_rays(sc, samples[i % 4])
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt / 1e6
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Mrays/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "shell1024: 1024^3 grid, 32^3 blocks, one 800x800 view (seeded quarter of its "
+                                   "rays per step)", "impl": "FP64 C oracle, OpenMP"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} seeded rays of the 800x800 view per step"},
+            "e2e": {"value": round(v, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------------------------
+# our arm
+# -------------------------------------------------------------------------------------
+def time_steps(fn, steps, warmup, stream, flush):
+    import torch
+    for _ in range(warmup):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2103_14645_gb300 import renderer, synth
+    dist = ws > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def flush():
+        flush_buf.fill_(1)
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    sc = synth.make_scene("shell1024")
+    cams = sc.cameras
+    if rank > 0:     # each rank renders its own seeded view of the same grid
+        cams = synth.orbit_cameras(np.random.default_rng(9000 + rank), [(800, 800)], synth.CAM_RADIUS)
+    r = renderer.Renderer.from_scene(sc, dev)
+    mlp = torch.from_numpy(sc.mlp).to(dev)
+    out = torch.empty((800 * 800, 3), dtype=torch.float32, device=dev)
+    n_rays = 800 * 800
+
+    # counted algorithmic bytes of one launch (untimed debug render)
+    dbg = r.render(cams, mlp, counts=True)
+    r.check_status()
+    cnt = dbg["counts"].double().sum(0).cpu().numpy()
+    steps_tot, active_tot, blocks_tot = cnt[0], cnt[1], cnt[2]
+    alg_bytes = 4 * blocks_tot + 1 * steps_tot + 64 * active_tot + 12 * n_rays
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    l0 = r.launches
+    ms = time_steps(lambda: r.render(cams, mlp, out=out), args.steps, args.warmup, stream, flush)
+    barrier()
+    launches = r.launches - l0 - args.warmup
+    t_step = float(np.mean(ms))
+    t_max = t_step
+    if dist:
+        t = torch.tensor([t_step], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = ws * n_rays / (t_max * 1e-3) / 1e6
+
+    # end to end through the public API with host buffers: camera record in, image out
+    host_out = torch.empty((n_rays, 3), dtype=torch.float32, pin_memory=True)
+
+    def e2e_step():
+        img = r.render(cams, mlp, out=out)
+        host_out.copy_(img, non_blocking=True)
+
+    barrier()
+    ms_e2e = time_steps(e2e_step, args.steps, args.warmup, stream, flush)
+    barrier()
+    e2e = ws * n_rays / (float(np.mean(ms_e2e)) * 1e-3) / 1e6
+
+    extra = {}
+    if not args.no_extra:
+        extra = extra_sections(args, r, sc, dev, stream, flush, barrier)
+    clocks = sampler.stop()
+
+    if rank != 0:
+        if dist:
+            tdist.destroy_process_group()
+        return
+    peaks, src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    achieved = alg_bytes / (t_step * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"shell1024: {sc.N}^3 grid, {sc.B}^3 blocks, {sc.occupancy * 100:.1f}% occupied "
+                               f"({sc.nb} blocks), one 800x800 view, 39 deg FOV",
+                   "l2": "flushed before every timed step (256 MiB write)", "launch": "plain (one launch per view)"},
+        "frames_per_s": round(1e3 / t_max, 2),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"{src} hbm_gbs", "kernel": "render_image_kernel",
+                     "algorithmic_bytes_per_launch": int(alg_bytes)},
+        "e2e": {"value": round(e2e, 3), "unit": "Mrays/s", "h2d_bytes_per_step": 80 * len(cams),
+                "d2h_bytes_per_step": n_rays * 12},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    line.update(extra)
+    if ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(sc)
+    print(json.dumps(line), flush=True)
+    if dist:
+        tdist.destroy_process_group()
+
+
+def extra_sections(args, r, sc, dev, stream, flush, barrier):
+    import torch
+    from paper_2103_14645_gb300 import renderer, synth
+    out = {}
+    # batched: 64 cameras of mixed resolutions on the same grid
+    bsc = synth.make_scene("batch1024")
+    cams = bsc.cameras
+    n_pix = bsc.n_pixels
+    mlp = torch.from_numpy(bsc.mlp).to(dev)
+    buf = torch.empty((n_pix, 3), dtype=torch.float32, device=dev)
+    reps = max(3, min(args.steps, 10))
+    barrier()
+    ms_b = time_steps(lambda: r.render(cams, mlp, out=buf, persistent=True), reps, 2, stream, flush)
+    ms_p = time_steps(lambda: r.render(cams, mlp, out=buf), reps, 2, stream, flush)
+    barrier()
+    tw, th, c = r.persistent_config()
+    out["batched"] = {"cameras": int(len(cams)), "rays": n_pix,
+                      "persistent_mrays_s": round(n_pix / (np.mean(ms_b) * 1e-3) / 1e6, 3),
+                      "plain_mrays_s": round(n_pix / (np.mean(ms_p) * 1e-3) / 1e6, 3),
+                      "ratio": round(float(np.mean(ms_p) / np.mean(ms_b)), 4),
+                      "tile": [tw, th], "ctas_per_sm": c,
+                      "ms_persistent": round(float(np.mean(ms_b)), 3), "ms_plain": round(float(np.mean(ms_p)), 3)}
+    del buf
+    # forward + backward of 65,536 rays on the 512^3 grid
+    wsc = synth.make_scene("bwd512")
+    rb = renderer.Renderer.from_scene(wsc, dev)
+    pix = torch.from_numpy(wsc.extra["pix"]).to(dev)
+    tgt = torch.from_numpy(wsc.extra["target"]).to(dev)
+    wm = torch.from_numpy(wsc.mlp).to(dev)
+    ga = torch.zeros(wsc.atlas.shape, dtype=torch.float32, device=dev)
+    gm = torch.zeros(883, dtype=torch.float32, device=dev)
+    c = torch.empty((pix.shape[0], 3), dtype=torch.float32, device=dev)
+
+    def fwd():
+        rb.render_rays(wsc.cameras, pix, wm, out=c)
+
+    def fwd_bwd():
+        rb.render_rays(wsc.cameras, pix, wm, out=c)
+        rb.backward(wsc.cameras, pix, wm, c - tgt, ga, gm)
+
+    ms_f = time_steps(fwd, reps, 2, stream, flush)
+    ms_fb = time_steps(fwd_bwd, reps, 2, stream, flush)
+    n = pix.shape[0]
+    out["fwd_bwd"] = {"workload": f"bwd512: {wsc.N}^3 grid, {wsc.occupancy * 100:.1f}% occupied, {n} rays over 8 views",
+                      "fwd_mrays_s": round(n / (np.mean(ms_f) * 1e-3) / 1e6, 3),
+                      "fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3),
+                      "ms_fwd": round(float(np.mean(ms_f)), 4), "ms_fwd_bwd": round(float(np.mean(ms_fb)), 4)}
+    return out
+
+
+def cpu_baseline(sc):
+    import oracle
+    from paper_2103_14645_gb300 import synth
+    pix = synth.all_pixels(sc.cameras)
+    oracle.render_rays(sc, pix[:1000])
+    t0 = time.perf_counter()
+    oracle.render_rays(sc, pix)
+    dt = time.perf_counter() - t0
+    return {"value": round(pix.shape[0] / dt / 1e6, 4), "unit": "Mrays/s", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": "the full 800x800 view once (640,000 rays), FP64 C oracle with OpenMP"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extra", action="store_true", help="headline workload only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * snerg.h -- C ABI of the GB300 renderer for baked Sparse Neural Radiance Grids
+ * (SNeRG, "Baking Neural Radiance Fields for Real-Time View Synthesis").
+ *
+ * The library renders the paper's baked representation (Sec. 5.1): an N^3 virtual
+ * voxel grid stored as an (N/B)^3 indirection grid whose entries are -1 (empty
+ * macroblock) or the slot of a B^3 macroblock in a uint8 atlas holding, per voxel,
+ * density, diffuse RGB and a 4-channel feature (Sec. 4.2, 8 bits each, Sec. 5.4).
+ * Each pixel's ray is marched through the grid (Sec. 5.2, App. A), composited with
+ * Eqs. 2, 5, 6, stopped once T < 1e-3, and finished with one evaluation of the
+ * view-dependence MLP (Eq. 7). A hand-written adjoint gives the gradients used to
+ * fine-tune the baked grid's view-dependent appearance (Sec. 5.5).
+ *
+ * Conventions for every entry point:
+ *   * Pointers prefixed d_ are DEVICE memory owned by the caller; h_ / unprefixed
+ *     struct pointers are HOST memory read during the call only. The library never
+ *     allocates device memory and never frees caller memory; its only device state is
+ *     the caller-provided workspace.
+ *   * Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) unless the entry point says it synchronises.
+ *   * Errors are return codes; nothing is thrown across the ABI. Errors found on the
+ *     device (a ray exceeding its iteration cap) are recorded in a status word in the
+ *     workspace and reported by snerg_last_status().
+ *   * A handle may be used from one host thread at a time.
+ *
+ * Arithmetic contract (what is bit-exact and what is not):
+ *   * integer decisions -- the sample lattice, the nearest voxel of each sample, the
+ *     block lookup, the density probe and the early-exit test -- are taken in IEEE
+ *     binary32 with one rounding per operation in a fixed order, so step counts and
+ *     visited voxels are reproducible bit for bit by an independent implementation;
+ *   * colours are accumulated in FP32 (max abs error vs FP64 well under 1e-4).
+ */
+#ifndef SNERG_H
+#define SNERG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SNERG_OK = 0,
+    SNERG_E_INVAL = 1,        /* invalid argument (sizes, pointers, indirection entries) */
+    SNERG_E_NOMEM = 2,        /* caller-provided buffer smaller than required */
+    SNERG_E_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    SNERG_E_STEP_LIMIT = 4,   /* device: a ray exceeded its iteration cap (4N + 16) */
+    SNERG_E_UNSUPPORTED = 5   /* request outside the compiled limits */
+} snerg_status;
+
+typedef struct snerg_scene* snerg_handle;
+
+/* Scene description (Sec. 5.1). World-space grid = axis-aligned cube
+ * [bmin, bmin + extent]^3; voxel width delta = extent / N. */
+typedef struct {
+    int32_t N;          /* virtual grid resolution per axis; 1 <= N <= 16384, N % B == 0 */
+    int32_t B;          /* macroblock edge; power of two in [2, 64] */
+    float bmin[3];      /* world-space minimum corner */
+    float extent;       /* world-space edge length, > 0 */
+    float sigma_max;    /* density of code 255 (1/world units): sigma = q / 255 * sigma_max */
+    float bg[3];        /* background colour, added with weight T_final */
+} snerg_scene_desc;
+
+/* Pinhole camera (Sec. 4.1 r(t) = o + t d). 80 bytes, host memory.
+ * Pixel (x, y) looks along R (x + 0.5 - cx) / fx, -(y + 0.5 - cy) / fy, -1) normalised,
+ * i.e. the camera looks down its -z axis with +y up and image rows growing downwards.
+ * Its RGB is written at out[(out_offset + y * W + x) * 3 + c]. */
+typedef struct {
+    float c2w[12];      /* row-major 3x4 camera-to-world [R | t] */
+    float fx, fy, cx, cy;
+    int32_t W, H;
+    int64_t out_offset; /* first output pixel of this camera */
+} snerg_camera;
+
+/* Optional per-call outputs and launch choices. All pointers nullable (device). */
+typedef struct {
+    float* d_aux;          /* [pixels][8]: C_d (3), V (4), accumulated opacity 1 - T */
+    int32_t* d_counts;     /* [pixels][4]: steps (lattice samples in occupied blocks), active
+                              (composited) samples, indirection entries read, 0 */
+    uint64_t* d_trace;     /* [pixels][trace_cap]: z*N*N + y*N + x of each composited sample */
+    int32_t trace_cap;
+    int32_t persistent;    /* snerg_render only: 1 = all cameras in one persistent launch,
+                              captured into a CUDA graph on first use and replayed */
+    int32_t tile_w, tile_h;/* persistent only: pixel tile per work item; 0 = autotune */
+    int32_t ctas_per_sm;   /* persistent only: 0 = autotune */
+} snerg_render_opts;
+
+/* Largest number of cameras in one snerg_render / ray-list call. */
+#define SNERG_MAX_CAMERAS 256
+/* Number of MLP parameters: W1[16][34], b1[16], W2[16][16], b2[16], W3[3][16], b3[3]
+ * (row-major, out x in), float32 (Eq. 7; "2 layers with 16 channels", Sec. 4.2). */
+#define SNERG_MLP_PARAMS 883
+
+/* Bytes of device workspace snerg_create needs for `num_blocks` occupied macroblocks;
+ * 0 if the description is invalid. The workspace holds the apron-padded device copy of
+ * the atlas, a density plane, the indirection grid and the status word. */
+size_t snerg_workspace_bytes(const snerg_scene_desc* desc, int64_t num_blocks);
+
+/* Build a scene handle (Sec. 5.1 data structure).
+ *   d_indirection : int32 [G][G][G] (z, y, x), G = N / B; each entry -1 or a slot in
+ *                   [0, num_blocks); no slot may be referenced twice.
+ *   d_atlas       : uint8 [num_blocks][B][B][B][8] (z, y, x, channel); channels
+ *                   density, r, g, b, f0, f1, f2, f3.
+ *   d_workspace   : >= snerg_workspace_bytes(desc, num_blocks) bytes, 256-byte
+ *                   aligned, owned by the caller and kept alive until snerg_destroy.
+ * Both inputs are copied into the workspace; the caller may free them afterwards.
+ * SYNCHRONISES `stream` (to validate the indirection grid). Returns SNERG_E_INVAL for
+ * a bad description, an out-of-range or repeated slot; SNERG_E_NOMEM if ws_bytes is
+ * too small. On error *out is NULL. */
+snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t* d_indirection,
+                          const uint8_t* d_atlas, int64_t num_blocks, void* d_workspace,
+                          size_t ws_bytes, void* stream, snerg_handle* out);
+
+/* Render every pixel of n_cams cameras (Sec. 5.2 and App. A; Eqs. 2, 5-7).
+ *   cams   : HOST array of n_cams (1..SNERG_MAX_CAMERAS) cameras, W, H >= 0.
+ *   d_mlp  : float32 [SNERG_MLP_PARAMS] view-dependence MLP weights.
+ *   d_rgb  : float32 output [total pixels][3] addressed through out_offset.
+ *   opts   : nullable. Debug outputs (aux, counts, trace) use the plain launch.
+ * The colour is C = C_d + sigmoid(MLP(C_d, V, PE(d))) + T bg if any sample was
+ * composited, else T bg (App. A evaluates the MLP only where alpha > 0). */
+snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
+                          const float* d_mlp, float* d_rgb, const snerg_render_opts* opts,
+                          void* stream);
+
+/* Render a list of rays: d_pix int32 [n][3] = (camera index, x, y). Output row i of
+ * d_rgb (and of the optional opts outputs) belongs to ray i; out_offset is ignored. */
+snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
+                               const int32_t* d_pix, int64_t n, const float* d_mlp,
+                               float* d_rgb, const snerg_render_opts* opts, void* stream);
+
+/* Adjoint of snerg_render_rays for an upstream gradient d_grad_rgb [n][3] = dL/dC
+ * (Sec. 5.5 fine-tunes against an L2 image loss, Eq. 3). Density is frozen. Each ray's
+ * march is recomputed instead of stored. ACCUMULATES (caller zeroes):
+ *   d_grad_atlas : float32 [num_blocks][B][B][B][8], dL/d(q/255) of channels 1..7 of
+ *                  every stored voxel; channel 0 (density) receives exactly zero;
+ *   d_grad_mlp   : float32 [SNERG_MLP_PARAMS].
+ * Either gradient pointer may be NULL to skip it. */
+snerg_status snerg_render_backward(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
+                                   const int32_t* d_pix, int64_t n, const float* d_mlp,
+                                   const float* d_grad_rgb, float* d_grad_atlas,
+                                   float* d_grad_mlp, void* stream);
+
+/* SYNCHRONISES `stream`, returns and clears the device status word (SNERG_OK or the
+ * first device error recorded since the last call), or SNERG_E_CUDA if the stream
+ * reports an asynchronous CUDA error. */
+snerg_status snerg_last_status(snerg_handle h, void* stream);
+
+/* Number of kernels the library launched through this handle since creation. */
+int64_t snerg_launch_count(snerg_handle h);
+
+/* Tile shape and CTAs/SM chosen by the last persistent launch (or 0s). */
+snerg_status snerg_persistent_config(snerg_handle h, int32_t* tile_w, int32_t* tile_h,
+                                     int32_t* ctas_per_sm);
+
+/* Release host state (cached graphs). Device memory is the caller's. NULL is allowed. */
+void snerg_destroy(snerg_handle h);
+
+/* Static string for a status code. */
+const char* snerg_status_str(snerg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNERG_H */

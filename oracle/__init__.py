@@ -81,8 +81,9 @@ def cameras_f32(cams) -> np.ndarray:
 
 
 def _scene_args(scene, val, mlp, cams):
+    # the scene description carries binary32 fields; read them at that precision
     bmin = np.asarray(scene.bmin, np.float32)
-    bg = np.asarray(scene.bg, np.float64)
+    bg = np.asarray(scene.bg, np.float32).astype(np.float64)
     ind = np.ascontiguousarray(scene.ind, np.int32)
     atlas = np.ascontiguousarray(scene.atlas, np.uint8)
     if val is not None:
@@ -92,7 +93,8 @@ def _scene_args(scene, val, mlp, cams):
     assert w.size == NPARAM
     cf = cameras_f32(scene.cameras if cams is None else cams)
     keep = (bmin, bg, ind, atlas, val, w, cf)
-    args = [int(scene.N), int(scene.B), _p(bmin), float(scene.extent), float(scene.sigma_max), _p(bg),
+    args = [int(scene.N), int(scene.B), _p(bmin), float(np.float32(scene.extent)),
+            float(np.float32(scene.sigma_max)), _p(bg),
             _p(ind), _p(atlas), _p(val), int(atlas.shape[0]), _p(w), _p(cf), int(cf.shape[0])]
     return args, keep
 

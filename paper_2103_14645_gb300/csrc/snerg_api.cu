@@ -1,0 +1,459 @@
+// snerg_api.cu -- host side of the C ABI declared in include/snerg.h.
+//
+// Validates arguments, lays out the caller's workspace, launches the kernels of
+// snerg_prep.cu / snerg_fwd.cu / snerg_bwd.cu on the caller's stream, and owns the
+// host state of the persistent multi-camera path: the autotuned launch shape and the
+// CUDA graphs (work-queue reset + persistent kernel) that are captured once per shape
+// and replayed with updated kernel parameters.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "snerg_internal.cuh"
+
+using namespace snerg;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+struct Layout {
+    size_t ind, blk, pdens, patlas, total;
+};
+
+int ilog2_exact(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return (1 << l) == v ? l : -1;
+}
+
+bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+bool desc_ok(const snerg_scene_desc* d) {
+    if (!d) return false;
+    if (d->N < 1 || d->N > 16384) return false;
+    if (d->B < 2 || d->B > 64 || ilog2_exact(d->B) < 0 || d->N % d->B != 0) return false;
+    if (d->N / d->B > 1024) return false;
+    if (!(std::isfinite(d->extent) && d->extent > 0.0f)) return false;
+    if (!(std::isfinite(d->sigma_max) && d->sigma_max >= 0.0f)) return false;
+    return finite3(d->bmin) && finite3(d->bg);
+}
+
+bool make_layout(const snerg_scene_desc* d, int64_t nb, Layout* L) {
+    if (!desc_ok(d) || nb < 0 || nb > (int64_t)1 << 31) return false;
+    const int64_t G = d->N / d->B;
+    const int64_t P = d->B + 2;
+    const size_t P3 = (size_t)(P * P * P);
+    L->ind = kAlign;                                          // [0, 256): header words
+    L->blk = align_up(L->ind + (size_t)(G * G * G) * 4);
+    L->pdens = align_up(L->blk + (size_t)nb * 4);
+    L->patlas = align_up(L->pdens + (size_t)nb * P3);
+    L->total = align_up(L->patlas + (size_t)nb * P3 * 8);
+    return true;
+}
+
+// header word indices (int32)
+constexpr int kHdrStatus = 0;
+constexpr int kHdrCreateErr = 1;
+constexpr int kHdrQueue = 16;    // own 64-byte line
+
+bool camera_ok(const snerg_camera& c) {
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(c.c2w[i])) return false;
+    if (!(std::isfinite(c.fx) && std::isfinite(c.fy) && std::isfinite(c.cx) && std::isfinite(c.cy))) return false;
+    if (c.fx == 0.0f || c.fy == 0.0f) return false;
+    if (c.W < 0 || c.H < 0 || c.out_offset < 0) return false;
+    return true;
+}
+
+struct PersistentConfig {
+    int warp_w, warp_h, passes, block, ctas_per_sm;
+    int tile_w() const { return warp_w; }
+    int tile_h() const { return warp_h * passes; }
+    bool operator<(const PersistentConfig& o) const {
+        return std::tie(warp_w, warp_h, passes, block, ctas_per_sm) <
+               std::tie(o.warp_w, o.warp_h, o.passes, o.block, o.ctas_per_sm);
+    }
+};
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t knode = nullptr;
+};
+
+}  // namespace
+
+struct snerg_scene {
+    snerg_scene_desc desc;
+    int64_t nb = 0;
+    DevScene ds;
+    uint8_t* ws = nullptr;
+    int32_t* hdr = nullptr;
+    int64_t launches = 0;
+    int num_sms = 1;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::vector<int32_t>, PersistentConfig> tuned;   // key: camera sizes
+    std::map<PersistentConfig, GraphEntry> graphs;
+    PersistentConfig last{0, 0, 0, 0, 0};
+};
+
+static snerg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SNERG_OK : SNERG_E_CUDA; }
+
+extern "C" size_t snerg_workspace_bytes(const snerg_scene_desc* desc, int64_t num_blocks) {
+    Layout L;
+    if (!make_layout(desc, num_blocks, &L)) return 0;
+    return L.total;
+}
+
+extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t* d_indirection,
+                                     const uint8_t* d_atlas, int64_t num_blocks, void* d_workspace,
+                                     size_t ws_bytes, void* stream, snerg_handle* out) {
+    if (!out) return SNERG_E_INVAL;
+    *out = nullptr;
+    Layout L;
+    if (!make_layout(desc, num_blocks, &L)) return SNERG_E_INVAL;
+    if (!d_indirection || !d_workspace) return SNERG_E_INVAL;
+    if (num_blocks > 0 && (!d_atlas || ((uintptr_t)d_atlas & 7u))) return SNERG_E_INVAL;
+    if ((uintptr_t)d_workspace & (kAlign - 1)) return SNERG_E_INVAL;
+    if (ws_bytes < L.total) return SNERG_E_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    snerg_scene* h = new (std::nothrow) snerg_scene();
+    if (!h) return SNERG_E_NOMEM;
+    h->desc = *desc;
+    h->nb = num_blocks;
+    h->ws = (uint8_t*)d_workspace;
+    h->hdr = (int32_t*)d_workspace;
+    const int N = desc->N, B = desc->B, G = N / B, P = B + 2;
+    const int64_t G3 = (int64_t)G * G * G;
+    int32_t* ws_ind = (int32_t*)(h->ws + L.ind);
+    int32_t* blk = (int32_t*)(h->ws + L.blk);
+    uint8_t* pdens = h->ws + L.pdens;
+    uint2* patlas = (uint2*)(h->ws + L.patlas);
+
+    cudaError_t e = cudaMemsetAsync(h->hdr, 0, kAlign, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws_ind, d_indirection, (size_t)G3 * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && num_blocks > 0) e = cudaMemsetAsync(blk, 0xff, (size_t)num_blocks * 4, st);
+    if (e == cudaSuccess) e = launch_validate(ws_ind, G3, num_blocks, blk, h->hdr + kHdrCreateErr, st);
+    int32_t err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->hdr + kHdrCreateErr, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { delete h; return SNERG_E_CUDA; }
+    if (err != 0) { delete h; return SNERG_E_INVAL; }
+    e = launch_build_padded(ws_ind, blk, d_atlas, num_blocks, N, B, ilog2_exact(B), pdens, patlas, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { delete h; return SNERG_E_CUDA; }
+    h->launches = 2;
+
+    DevScene& s = h->ds;
+    s.ind = ws_ind;
+    s.pdens = pdens;
+    s.patlas = patlas;
+    s.status = h->hdr + kHdrStatus;
+    s.N = N;
+    s.B = B;
+    s.lgB = ilog2_exact(B);
+    s.G = G;
+    s.P = P;
+    s.P3 = P * P * P;
+    s.fN = (float)N;
+    s.scale = (float)N / desc->extent;
+    for (int i = 0; i < 3; ++i) {
+        s.bmin[i] = desc->bmin[i];
+        s.bg[i] = desc->bg[i];
+    }
+    s.kappa = (float)((double)desc->sigma_max * ((double)desc->extent / (double)N) / 255.0);
+    s.taumax = (float)std::log(1000.0);
+    s.kmax = 4 * N + 16;
+
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (h->num_sms < 1) h->num_sms = 1;
+    *out = h;
+    return SNERG_OK;
+}
+
+static bool opts_debug(const snerg_render_opts* o) {
+    return o && (o->d_aux || o->d_counts || (o->d_trace && o->trace_cap > 0));
+}
+
+static DebugOut make_dbg(const snerg_render_opts* o) {
+    DebugOut d{nullptr, nullptr, nullptr, 0};
+    if (o) {
+        d.aux = o->d_aux;
+        d.counts = o->d_counts;
+        if (o->d_trace && o->trace_cap > 0) {
+            d.trace = o->d_trace;
+            d.trace_cap = o->trace_cap;
+        }
+    }
+    return d;
+}
+
+// ---------------------------------------------------------------------------------
+// persistent multi-camera path
+// ---------------------------------------------------------------------------------
+static void fill_params(PersistentParams& p, const snerg_camera* cams, int32_t n, const PersistentConfig& c) {
+    std::memset(&p, 0, sizeof(p));
+    p.n_cams = n;
+    p.tile_w = c.tile_w();
+    p.tile_h = c.tile_h();
+    p.warp_w = c.warp_w;
+    p.warp_h = c.warp_h;
+    int32_t acc = 0;
+    for (int i = 0; i < n; ++i) {
+        p.cams[i] = cams[i];
+        const int tx = (cams[i].W + p.tile_w - 1) / p.tile_w;
+        const int ty = (cams[i].H + p.tile_h - 1) / p.tile_h;
+        p.tiles_x[i] = tx > 0 ? tx : 1;
+        p.tile_start[i] = acc;
+        acc += (cams[i].W > 0 && cams[i].H > 0) ? tx * ty : 0;
+    }
+    p.tile_start[n] = acc;
+    p.total_items = acc;
+}
+
+static cudaError_t launch_persistent_direct(snerg_scene* h, const PersistentParams& p, const PersistentConfig& c,
+                                            const float* mlp, float* rgb, cudaStream_t st) {
+    int32_t* queue = h->hdr + kHdrQueue;
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    h->launches++;
+    return launch_render_persistent(h->ds, p, mlp, rgb, queue, h->num_sms * c.ctas_per_sm, c.block, st);
+}
+
+static PersistentConfig autotune(snerg_scene* h, const snerg_camera* cams, int32_t n, const float* mlp, float* rgb,
+                                 cudaStream_t st) {
+    static const int shapes[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
+    static const int passes[2] = {1, 4};
+    static const int ctas[2] = {4, 8};
+    std::vector<PersistentConfig> cand;
+    for (auto& s : shapes)
+        for (int ps : passes)
+            for (int c : ctas) cand.push_back(PersistentConfig{s[0], s[1], ps, 128, c});
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    PersistentConfig best = cand[0];
+    float best_ms = 1e30f;
+    PersistentParams* p = new PersistentParams;
+    for (const auto& c : cand) {
+        fill_params(*p, cams, n, c);
+        if (launch_persistent_direct(h, *p, c, mlp, rgb, st) != cudaSuccess) continue;   // warm-up
+        cudaEventRecord(e0, st);
+        if (launch_persistent_direct(h, *p, c, mlp, rgb, st) != cudaSuccess) continue;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    delete p;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+static snerg_status render_persistent(snerg_scene* h, const snerg_camera* cams, int32_t n, const float* mlp,
+                                      float* rgb, const snerg_render_opts* o, cudaStream_t st) {
+    PersistentConfig cfg{0, 0, 0, 128, 0};
+    const bool manual = o && o->tile_w > 0 && o->tile_h > 0 && o->ctas_per_sm > 0;
+    if (manual) {
+        // tile_w x tile_h with tile_w dividing 32 (a warp pass is tile_w x (32 / tile_w))
+        if (32 % o->tile_w != 0 || o->tile_h % (32 / o->tile_w) != 0 || o->ctas_per_sm > 16)
+            return SNERG_E_INVAL;
+        cfg.warp_w = o->tile_w;
+        cfg.warp_h = 32 / o->tile_w;
+        cfg.passes = o->tile_h / cfg.warp_h;
+        cfg.ctas_per_sm = o->ctas_per_sm;
+    } else {
+        std::vector<int32_t> key;
+        for (int i = 0; i < n; ++i) {
+            key.push_back(cams[i].W);
+            key.push_back(cams[i].H);
+        }
+        auto it = h->tuned.find(key);
+        if (it == h->tuned.end()) it = h->tuned.emplace(key, autotune(h, cams, n, mlp, rgb, st)).first;
+        cfg = it->second;
+    }
+    h->last = cfg;
+    PersistentParams* p = new (std::nothrow) PersistentParams;
+    if (!p) return SNERG_E_NOMEM;
+    fill_params(*p, cams, n, cfg);
+    const int grid = h->num_sms * cfg.ctas_per_sm;
+    int32_t* queue = h->hdr + kHdrQueue;
+    GraphEntry& ge = h->graphs[cfg];
+    cudaError_t e = cudaSuccess;
+    if (!ge.exec) {
+        if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(queue, 0, sizeof(int32_t), h->cap_stream);
+            launch_render_persistent(h->ds, *p, mlp, rgb, queue, grid, cfg.block, h->cap_stream);
+            e = cudaStreamEndCapture(h->cap_stream, &ge.graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
+        if (e == cudaSuccess) {
+            size_t cnt = 0;
+            cudaGraphGetNodes(ge.graph, nullptr, &cnt);
+            std::vector<cudaGraphNode_t> nodes(cnt);
+            cudaGraphGetNodes(ge.graph, nodes.data(), &cnt);
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                cudaGraphNodeGetType(nd, &t);
+                if (t == cudaGraphNodeTypeKernel) ge.knode = nd;
+            }
+            if (!ge.knode) e = cudaErrorUnknown;
+        }
+        if (e != cudaSuccess) {
+            if (ge.exec) cudaGraphExecDestroy(ge.exec);
+            if (ge.graph) cudaGraphDestroy(ge.graph);
+            h->graphs.erase(cfg);
+            delete p;
+            return SNERG_E_CUDA;
+        }
+    }
+    // refresh the kernel node with this call's cameras and buffers, then replay
+    DevScene ds = h->ds;
+    const float* mlp_arg = mlp;
+    float* rgb_arg = rgb;
+    void* args[] = {(void*)&ds, (void*)p, (void*)&mlp_arg, (void*)&rgb_arg, (void*)&queue};
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = const_cast<void*>(persistent_kernel_fn());
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(cfg.block);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    e = cudaGraphExecKernelNodeSetParams(ge.exec, ge.knode, &kp);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge.exec, st);
+    delete p;
+    if (e != cudaSuccess) return SNERG_E_CUDA;
+    h->launches++;
+    return SNERG_OK;
+}
+
+extern "C" snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, int32_t n_cams, const float* d_mlp,
+                                     float* d_rgb, const snerg_render_opts* opts, void* stream) {
+    if (!h || !cams || n_cams < 1 || n_cams > kMaxCams) return SNERG_E_INVAL;
+    int64_t pixels = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        if (!camera_ok(cams[i])) return SNERG_E_INVAL;
+        pixels += (int64_t)cams[i].W * cams[i].H;
+    }
+    if (pixels == 0) return SNERG_OK;
+    if (!d_mlp || !d_rgb) return SNERG_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (opts && opts->persistent && !opts_debug(opts)) return render_persistent(h, cams, n_cams, d_mlp, d_rgb, opts, st);
+    const DebugOut dbg = make_dbg(opts);
+    for (int i = 0; i < n_cams; ++i) {
+        if (cams[i].W == 0 || cams[i].H == 0) continue;
+        cudaError_t e = launch_render_image(h->ds, cams[i], d_mlp, d_rgb, dbg, st);
+        if (e != cudaSuccess) return SNERG_E_CUDA;
+        h->launches++;
+    }
+    return SNERG_OK;
+}
+
+static bool make_table(const snerg_camera* cams, int32_t n_cams, CamTable* t) {
+    if (!cams || n_cams < 1 || n_cams > kMaxCams) return false;
+    std::memset(t, 0, sizeof(*t));
+    for (int i = 0; i < n_cams; ++i) {
+        if (!camera_ok(cams[i])) return false;
+        t->c[i] = cams[i];
+    }
+    return true;
+}
+
+extern "C" snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
+                                          const int32_t* d_pix, int64_t n, const float* d_mlp, float* d_rgb,
+                                          const snerg_render_opts* opts, void* stream) {
+    if (!h || n < 0) return SNERG_E_INVAL;
+    CamTable* t = new (std::nothrow) CamTable;
+    if (!t) return SNERG_E_NOMEM;
+    if (!make_table(cams, n_cams, t)) { delete t; return SNERG_E_INVAL; }
+    if (n == 0) { delete t; return SNERG_OK; }
+    if (!d_pix || !d_mlp || !d_rgb) { delete t; return SNERG_E_INVAL; }
+    cudaError_t e = launch_render_rays(h->ds, *t, n_cams, d_pix, n, d_mlp, d_rgb, make_dbg(opts), (cudaStream_t)stream);
+    delete t;
+    if (e != cudaSuccess) return SNERG_E_CUDA;
+    h->launches++;
+    return SNERG_OK;
+}
+
+extern "C" snerg_status snerg_render_backward(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
+                                              const int32_t* d_pix, int64_t n, const float* d_mlp,
+                                              const float* d_grad_rgb, float* d_grad_atlas, float* d_grad_mlp,
+                                              void* stream) {
+    if (!h || n < 0) return SNERG_E_INVAL;
+    CamTable* t = new (std::nothrow) CamTable;
+    if (!t) return SNERG_E_NOMEM;
+    if (!make_table(cams, n_cams, t)) { delete t; return SNERG_E_INVAL; }
+    if (n == 0 || (!d_grad_atlas && !d_grad_mlp)) { delete t; return SNERG_OK; }
+    if (!d_pix || !d_mlp || !d_grad_rgb) { delete t; return SNERG_E_INVAL; }
+    if (d_grad_atlas && ((uintptr_t)d_grad_atlas & 15u)) { delete t; return SNERG_E_INVAL; }
+    cudaError_t e = launch_backward_rays(h->ds, *t, n_cams, d_pix, n, d_mlp, d_grad_rgb, d_grad_atlas, d_grad_mlp,
+                                         (cudaStream_t)stream);
+    delete t;
+    if (e != cudaSuccess) return SNERG_E_CUDA;
+    h->launches++;
+    return SNERG_OK;
+}
+
+extern "C" snerg_status snerg_last_status(snerg_handle h, void* stream) {
+    if (!h) return SNERG_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t v = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, h->hdr + kHdrStatus, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->hdr + kHdrStatus, 0, 4, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return SNERG_E_CUDA;
+    return (snerg_status)v;
+}
+
+extern "C" int64_t snerg_launch_count(snerg_handle h) { return h ? h->launches : 0; }
+
+extern "C" snerg_status snerg_persistent_config(snerg_handle h, int32_t* tile_w, int32_t* tile_h,
+                                                int32_t* ctas_per_sm) {
+    if (!h || !tile_w || !tile_h || !ctas_per_sm) return SNERG_E_INVAL;
+    *tile_w = h->last.warp_w ? h->last.tile_w() : 0;
+    *tile_h = h->last.warp_w ? h->last.tile_h() : 0;
+    *ctas_per_sm = h->last.ctas_per_sm;
+    return SNERG_OK;
+}
+
+extern "C" void snerg_destroy(snerg_handle h) {
+    if (!h) return;
+    for (auto& kv : h->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+extern "C" const char* snerg_status_str(snerg_status s) {
+    switch (s) {
+        case SNERG_OK: return "ok";
+        case SNERG_E_INVAL: return "invalid argument";
+        case SNERG_E_NOMEM: return "buffer too small";
+        case SNERG_E_CUDA: return "CUDA error";
+        case SNERG_E_STEP_LIMIT: return "a ray exceeded its iteration cap";
+        case SNERG_E_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}

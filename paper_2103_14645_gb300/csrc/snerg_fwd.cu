@@ -1,0 +1,164 @@
+// snerg_fwd.cu -- forward render kernels: one camera per launch, ray lists, and the
+// persistent multi-camera kernel that drains a (camera, tile) work queue.
+// The per-ray arithmetic is in snerg_internal.cuh (Sec. 5.2, App. A; Eqs. 2, 5-7).
+#include "snerg_internal.cuh"
+
+namespace snerg {
+
+// Warp w of a 128-thread CTA covers an 8x4 pixel packet of the CTA's 16x8 tile, so the
+// 32 rays of a warp are neighbours on screen and walk neighbouring voxels together.
+template <bool DBG>
+__global__ void __launch_bounds__(128) render_image_kernel(const DevScene s, const snerg_camera cam,
+                                                           const float* __restrict__ mlp,
+                                                           float* __restrict__ rgb, const DebugOut dbg) {
+    __shared__ float sW[kNParam];
+    load_mlp_smem(sW, mlp);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    if (px >= cam.W || py >= cam.H) return;
+    const Ray r = make_ray(s, cam, px, py);
+    const int64_t pix = cam.out_offset + (int64_t)py * cam.W + px;
+    MarchState st;
+    if (DBG && dbg.trace)
+        march<true, false>(s, r, st, dbg.trace + pix * dbg.trace_cap, dbg.trace_cap, nullptr, nullptr);
+    else
+        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
+    record_status(s, st);
+    float c[3], aux[kAuxCh];
+    finish_ray(s, sW, r, st, c, aux);
+    rgb[pix * 3 + 0] = c[0];
+    rgb[pix * 3 + 1] = c[1];
+    rgb[pix * 3 + 2] = c[2];
+    if (DBG) {
+        if (dbg.aux)
+            for (int k = 0; k < kAuxCh; ++k) dbg.aux[pix * kAuxCh + k] = aux[k];
+        if (dbg.counts) {
+            dbg.counts[pix * 4] = st.steps;
+            dbg.counts[pix * 4 + 1] = st.active;
+            dbg.counts[pix * 4 + 2] = st.blocks;
+            dbg.counts[pix * 4 + 3] = 0;
+        }
+    }
+}
+
+template <bool DBG>
+__global__ void __launch_bounds__(128) render_rays_kernel(const DevScene s, const __grid_constant__ CamTable cams,
+                                                          int32_t n_cams, const int32_t* __restrict__ pix,
+                                                          int64_t n, const float* __restrict__ mlp,
+                                                          float* __restrict__ rgb, const DebugOut dbg) {
+    __shared__ float sW[kNParam];
+    load_mlp_smem(sW, mlp);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ci = __ldg(pix + 3 * i), px = __ldg(pix + 3 * i + 1), py = __ldg(pix + 3 * i + 2);
+    Ray r;
+    if (ci >= 0 && ci < n_cams && px >= 0 && py >= 0 && px < cams.c[ci].W && py < cams.c[ci].H) {
+        r = make_ray(s, cams.c[ci], px, py);
+    } else {
+        r.hit = false;
+        r.d[0] = r.d[1] = r.d[2] = 0.0f;
+        atomicCAS(s.status, 0, (int)SNERG_E_INVAL);
+    }
+    MarchState st;
+    if (DBG && dbg.trace)
+        march<true, false>(s, r, st, dbg.trace + i * dbg.trace_cap, dbg.trace_cap, nullptr, nullptr);
+    else
+        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
+    record_status(s, st);
+    float c[3], aux[kAuxCh];
+    finish_ray(s, sW, r, st, c, aux);
+    rgb[i * 3 + 0] = c[0];
+    rgb[i * 3 + 1] = c[1];
+    rgb[i * 3 + 2] = c[2];
+    if (DBG) {
+        if (dbg.aux)
+            for (int k = 0; k < kAuxCh; ++k) dbg.aux[i * kAuxCh + k] = aux[k];
+        if (dbg.counts) {
+            dbg.counts[i * 4] = st.steps;
+            dbg.counts[i * 4 + 1] = st.active;
+            dbg.counts[i * 4 + 2] = st.blocks;
+            dbg.counts[i * 4 + 3] = 0;
+        }
+    }
+}
+
+// Persistent multi-camera render: gridDim = SMs x CTAs/SM. Each warp pulls work items
+// (tile_w x tile_h pixels of one camera) from a global counter until the queue is empty,
+// and renders each item in warp_w x warp_h packets of 32 rays. The counter is zeroed by
+// the launch sequence (a memset node of the captured graph) before every launch.
+__global__ void __launch_bounds__(256) render_persistent_kernel(const DevScene s,
+                                                                const __grid_constant__ PersistentParams p,
+                                                                const float* __restrict__ mlp,
+                                                                float* __restrict__ rgb,
+                                                                int32_t* __restrict__ queue) {
+    __shared__ float sW[kNParam];
+    load_mlp_smem(sW, mlp);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int passes_x = p.tile_w / p.warp_w;
+    const int passes = passes_x * (p.tile_h / p.warp_h);
+    const int lx = lane % p.warp_w, ly = lane / p.warp_w;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(queue, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= p.total_items) break;
+        int lo = 0, hi = p.n_cams;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (p.tile_start[mid] <= item) lo = mid; else hi = mid;
+        }
+        const snerg_camera& cam = p.cams[lo];
+        const int rem = item - p.tile_start[lo];
+        const int tx = rem % p.tiles_x[lo], ty = rem / p.tiles_x[lo];
+        for (int ps = 0; ps < passes; ++ps) {
+            const int px = tx * p.tile_w + (ps % passes_x) * p.warp_w + lx;
+            const int py = ty * p.tile_h + (ps / passes_x) * p.warp_h + ly;
+            if (px < cam.W && py < cam.H) {
+                const Ray r = make_ray(s, cam, px, py);
+                MarchState st;
+                march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
+                record_status(s, st);
+                float c[3], aux[kAuxCh];
+                finish_ray(s, sW, r, st, c, aux);
+                const int64_t o = (cam.out_offset + (int64_t)py * cam.W + px) * 3;
+                rgb[o + 0] = c[0];
+                rgb[o + 1] = c[1];
+                rgb[o + 2] = c[2];
+            }
+        }
+    }
+}
+
+cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, float* rgb,
+                                const DebugOut& dbg, cudaStream_t st) {
+    if (cam.W <= 0 || cam.H <= 0) return cudaSuccess;
+    dim3 grid((cam.W + 15) / 16, (cam.H + 7) / 8);
+    const bool d = dbg.aux || dbg.counts || dbg.trace;
+    if (d) render_image_kernel<true><<<grid, 128, 0, st>>>(s, cam, mlp, rgb, dbg);
+    else render_image_kernel<false><<<grid, 128, 0, st>>>(s, cam, mlp, rgb, dbg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
+                               int64_t n, const float* mlp, float* rgb, const DebugOut& dbg, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    const bool d = dbg.aux || dbg.counts || dbg.trace;
+    if (d) render_rays_kernel<true><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, rgb, dbg);
+    else render_rays_kernel<false><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, rgb, dbg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_persistent(const DevScene& s, const PersistentParams& p, const float* mlp, float* rgb,
+                                     int32_t* queue, int grid, int block, cudaStream_t st) {
+    render_persistent_kernel<<<grid, block, 0, st>>>(s, p, mlp, rgb, queue);
+    return cudaGetLastError();
+}
+
+const void* persistent_kernel_fn() { return (const void*)render_persistent_kernel; }
+
+}  // namespace snerg

@@ -1,0 +1,440 @@
+// snerg_internal.cuh -- device-side core of the SNeRG renderer (sm_103a).
+//
+// Per pixel: pinhole ray (Sec. 4.1), clip to the grid, march the macroblock
+// indirection grid skipping empty blocks (Sec. 5.1-5.2, App. A), probe the nearest
+// voxel's density and fetch/interpolate all 8 channels only where it is non-zero
+// (App. A), alpha-composite diffuse colour and features (Eqs. 2, 5, 6), stop once the
+// optical depth exceeds ln(1000) (T < 1e-3; "terminating ray-marching once the opacity
+// has saturated", Sec. 5.2), then one evaluation of the view-dependence MLP (Eq. 7).
+//
+// Integer decisions (sample lattice, nearest voxel, block membership, early exit) use
+// IEEE binary32 with one rounding per operation, written with __fadd_rn/__fmul_rn/...
+// so nvcc cannot contract them into FMAs; the operation order is part of the renderer's
+// arithmetic contract (include/snerg.h) and makes step counts and visited voxels
+// reproducible bit for bit. Colour arithmetic is ordinary FP32.
+//
+// Device layout (built by snerg_prep.cu inside the caller's workspace):
+//   ind    int32 [G^3]                 indirection, -1 = empty (z, y, x)
+//   pdens  uint8 [nb][P^3], P = B + 2  density codes of each block with a 1-voxel apron
+//   patlas uint2 [nb][P^3]             all 8 channels (density, r, g, b | f0..f3)
+// The apron holds the neighbouring blocks' voxels (0 where the neighbour is empty) and
+// the clamped edge voxel at the grid border, so every trilinear stencil of a sample
+// whose nearest voxel lies in block b reads only block b's padded copy.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "snerg.h"
+
+namespace snerg {
+
+constexpr int kMlpIn = 34;
+constexpr int kMlpH = 16;
+constexpr int kMlpOut = 3;
+constexpr int kNParam = 883;
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kMlpH * kMlpIn;
+constexpr int kOffW2 = kOffB1 + kMlpH;
+constexpr int kOffB2 = kOffW2 + kMlpH * kMlpH;
+constexpr int kOffW3 = kOffB2 + kMlpH;
+constexpr int kOffB3 = kOffW3 + kMlpOut * kMlpH;
+static_assert(kOffB3 + kMlpOut == kNParam, "MLP layout");
+
+constexpr int kMaxCams = SNERG_MAX_CAMERAS;
+constexpr int kAuxCh = 8;
+
+// device status word bits
+constexpr int kStatusStepLimit = SNERG_E_STEP_LIMIT;
+
+struct DevScene {
+    const int32_t* ind;
+    const uint8_t* pdens;
+    const uint2* patlas;
+    int32_t* status;
+    int32_t N, B, lgB, G, P, P3;
+    float fN;         // (float)N
+    float scale;      // binary32(N / extent)
+    float bmin[3];
+    float kappa;      // binary32(sigma_max * extent / N / 255): optical depth per density code
+    float taumax;     // binary32(ln 1000)
+    float bg[3];
+    int32_t kmax;     // lattice index cap (4N + 16)
+};
+
+struct CamTable {
+    snerg_camera c[kMaxCams];
+};
+
+struct Ray {
+    float o[3];
+    float d[3];
+    float t0, t1;
+    bool hit;
+};
+
+struct MarchState {
+    float acc[7];     // sum_k w_k * (sum_corners tw * code) for channels 1..7 (codes, not /255)
+    float T;
+    float tau;
+    int steps;
+    int active;
+    int blocks;       // indirection entries read
+    bool limit;
+};
+
+// ---------------------------------------------------------------------------------
+// ray generation and clipping (binary32, fixed order)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ Ray make_ray(const DevScene& s, const snerg_camera& c, int px, int py) {
+    Ray r;
+    const float xs = __fdiv_rn(__fsub_rn(__fadd_rn((float)px, 0.5f), c.cx), c.fx);
+    const float ys = __fdiv_rn(__fsub_rn(__fadd_rn((float)py, 0.5f), c.cy), c.fy);
+    const float dc0 = xs, dc1 = -ys, dc2 = -1.0f;
+    float d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        d[i] = __fadd_rn(__fadd_rn(__fmul_rn(c.c2w[4 * i], dc0), __fmul_rn(c.c2w[4 * i + 1], dc1)),
+                         __fmul_rn(c.c2w[4 * i + 2], dc2));
+    const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])), __fmul_rn(d[2], d[2]));
+    const float nrm = __fsqrt_rn(n2);
+    float tn = -INFINITY, tf = INFINITY;
+    r.hit = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        r.d[i] = __fdiv_rn(d[i], nrm);
+        r.o[i] = __fmul_rn(__fsub_rn(c.c2w[4 * i + 3], s.bmin[i]), s.scale);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (r.d[i] != 0.0f) {
+            const float ta = __fdiv_rn(-r.o[i], r.d[i]);
+            const float tb = __fdiv_rn(__fsub_rn(s.fN, r.o[i]), r.d[i]);
+            tn = fmaxf(tn, fminf(ta, tb));
+            tf = fminf(tf, fmaxf(ta, tb));
+        } else if (r.o[i] < 0.0f || r.o[i] > s.fN) {
+            r.hit = false;
+        }
+    }
+    r.t0 = fmaxf(tn, 0.0f);
+    r.t1 = tf;
+    if (!(r.t0 < r.t1)) r.hit = false;
+    return r;
+}
+
+__device__ __forceinline__ float lattice_t(const Ray& r, int k) {
+    return __fadd_rn(r.t0, __fadd_rn((float)k, 0.5f));
+}
+
+__device__ __forceinline__ float lattice_u(const Ray& r, float t, int i) {
+    return __fadd_rn(r.o[i], __fmul_rn(t, r.d[i]));
+}
+
+__device__ __forceinline__ int nearest_voxel(float u, int N) {
+    return min(max((int)floorf(u), 0), N - 1);
+}
+
+// true iff sample k lies before the ray's exit and its nearest voxel is in block b
+__device__ __forceinline__ bool in_block(const DevScene& s, const Ray& r, int k, const int b[3]) {
+    const float t = lattice_t(r, k);
+    if (!(t < r.t1)) return false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        if ((nearest_voxel(lattice_u(r, t, i), s.N) >> s.lgB) != b[i]) return false;
+    return true;
+}
+
+// First lattice index k' > k with in_block(k') false. Each axis's nearest voxel is a
+// monotone function of k (every step of the lattice arithmetic is a rounded monotone
+// operation), so the samples of one block form a contiguous run: estimate its end from
+// the ray/box exit distance, then confirm or correct with an exact search.
+__device__ __forceinline__ int block_exit(const DevScene& s, const Ray& r, int k, const int b[3]) {
+    float te = INFINITY;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (r.d[i] > 0.0f) te = fminf(te, ((float)((b[i] + 1) << s.lgB) - r.o[i]) / r.d[i]);
+        else if (r.d[i] < 0.0f) te = fminf(te, ((float)(b[i] << s.lgB) - r.o[i]) / r.d[i]);
+    }
+    te = fminf(te, r.t1);
+    float kf = ceilf(te - r.t0 - 0.5f);
+    int ke = (kf > (float)s.kmax) ? s.kmax : (int)kf;
+    ke = max(ke, k + 1);
+    int lo = k, hi;
+    if (ke - 1 > k && !in_block(s, r, ke - 1, b)) {
+        hi = ke - 1;
+    } else if (ke < s.kmax && in_block(s, r, ke, b)) {
+        lo = ke;
+        int step = 1;
+        for (;;) {
+            hi = lo + step;
+            if (hi >= s.kmax) { hi = s.kmax; break; }
+            if (!in_block(s, r, hi, b)) break;
+            lo = hi;
+            step <<= 1;
+        }
+    } else {
+        return ke;
+    }
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (in_block(s, r, mid, b)) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+__device__ __forceinline__ float code(uint32_t w, int byte) {
+    return (float)((w >> (8 * byte)) & 0xffu);
+}
+
+// ---------------------------------------------------------------------------------
+// the march. TRACE records visited voxels; GRAD scatters w_k * trilinear weight * g
+// into the gradient atlas (density frozen, so the weights are the forward ones).
+// ---------------------------------------------------------------------------------
+template <bool TRACE, bool GRAD>
+__device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchState& st,
+                                      uint64_t* trace, int trace_cap,
+                                      const float* gfeat, float* grad_atlas) {
+#pragma unroll
+    for (int c = 0; c < 7; ++c) st.acc[c] = 0.0f;
+    st.T = 1.0f;
+    st.tau = 0.0f;
+    st.steps = 0;
+    st.active = 0;
+    st.blocks = 0;
+    st.limit = false;
+    if (!r.hit) return;
+    const int N = s.N, B = s.B, P = s.P;
+    int k = 0;
+    for (;;) {
+        if (k >= s.kmax) { st.limit = true; return; }
+        const float t = lattice_t(r, k);
+        if (!(t < r.t1)) return;
+        int b[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) b[i] = nearest_voxel(lattice_u(r, t, i), N) >> s.lgB;
+        const int slot = __ldg(s.ind + ((b[2] * s.G + b[1]) * s.G + b[0]));
+        st.blocks++;
+        const int kx = block_exit(s, r, k, b);
+        if (slot >= 0) {
+            const uint8_t* pd = s.pdens + (size_t)slot * s.P3;
+            const uint2* pa = s.patlas + (size_t)slot * s.P3;
+            const int ox = (b[0] << s.lgB) - 1, oy = (b[1] << s.lgB) - 1, oz = (b[2] << s.lgB) - 1;
+            for (int kk = k; kk < kx; ++kk) {
+                st.steps++;
+                const float tk = lattice_t(r, kk);
+                float u[3];
+                int j[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    u[i] = lattice_u(r, tk, i);
+                    j[i] = nearest_voxel(u[i], N);
+                }
+                // j lies in block b for every kk < kx (block_exit), i.e. l in [1, B]; the
+                // clamp only guards the address
+                const int lx = min(max(j[0] - ox, 1), B), ly = min(max(j[1] - oy, 1), B),
+                          lz = min(max(j[2] - oz, 1), B);
+                const uint8_t qn = __ldg(pd + (lz * P + ly) * P + lx);
+                if (qn == 0) continue;
+                if (TRACE && st.active < trace_cap)
+                    trace[st.active] = ((uint64_t)j[2] * N + (uint64_t)j[1]) * N + (uint64_t)j[0];
+                st.active++;
+                // trilinear stencil on the virtual grid, cell-centred
+                float f[3], g[3];
+                int l0[3];
+                float fl[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float x = __fsub_rn(u[i], 0.5f);
+                    fl[i] = floorf(x);
+                    f[i] = __fsub_rn(x, fl[i]);
+                    g[i] = __fsub_rn(1.0f, f[i]);
+                }
+                l0[0] = min(max((int)fl[0] - ox, 0), B);
+                l0[1] = min(max((int)fl[1] - oy, 0), B);
+                l0[2] = min(max((int)fl[2] - oz, 0), B);
+                const uint2* p0 = pa + (l0[2] * P + l0[1]) * P + l0[0];
+                const int PP = P * P;
+                uint2 cv[8];   // index = z*4 + y*2 + x
+                cv[0] = __ldg(p0);
+                cv[1] = __ldg(p0 + 1);
+                cv[2] = __ldg(p0 + P);
+                cv[3] = __ldg(p0 + P + 1);
+                cv[4] = __ldg(p0 + PP);
+                cv[5] = __ldg(p0 + PP + 1);
+                cv[6] = __ldg(p0 + PP + P);
+                cv[7] = __ldg(p0 + PP + P + 1);
+                // binary32 control: density trilinear, x then y then z
+                const float e00 = __fadd_rn(__fmul_rn(code(cv[0].x, 0), g[0]), __fmul_rn(code(cv[1].x, 0), f[0]));
+                const float e10 = __fadd_rn(__fmul_rn(code(cv[2].x, 0), g[0]), __fmul_rn(code(cv[3].x, 0), f[0]));
+                const float e01 = __fadd_rn(__fmul_rn(code(cv[4].x, 0), g[0]), __fmul_rn(code(cv[5].x, 0), f[0]));
+                const float e11 = __fadd_rn(__fmul_rn(code(cv[6].x, 0), g[0]), __fmul_rn(code(cv[7].x, 0), f[0]));
+                const float e0 = __fadd_rn(__fmul_rn(e00, g[1]), __fmul_rn(e10, f[1]));
+                const float e1 = __fadd_rn(__fmul_rn(e01, g[1]), __fmul_rn(e11, f[1]));
+                const float sq = __fadd_rn(__fmul_rn(e0, g[2]), __fmul_rn(e1, f[2]));
+                const float od = __fmul_rn(sq, s.kappa);
+                st.tau = __fadd_rn(st.tau, od);
+                // compositing (Eqs. 2, 5, 6)
+                const float e = expf(-od);
+                const float wk = st.T * (1.0f - e);
+                st.T *= e;
+                float tw[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    tw[c] = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float w = wk * tw[c];
+                    st.acc[0] += w * code(cv[c].x, 1);
+                    st.acc[1] += w * code(cv[c].x, 2);
+                    st.acc[2] += w * code(cv[c].x, 3);
+                    st.acc[3] += w * code(cv[c].y, 0);
+                    st.acc[4] += w * code(cv[c].y, 1);
+                    st.acc[5] += w * code(cv[c].y, 2);
+                    st.acc[6] += w * code(cv[c].y, 3);
+                }
+                if (GRAD) {
+                    const int B3 = B * B * B;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int X = min(max((int)fl[0] + (c & 1), 0), N - 1);
+                        const int Y = min(max((int)fl[1] + ((c >> 1) & 1), 0), N - 1);
+                        const int Z = min(max((int)fl[2] + ((c >> 2) & 1), 0), N - 1);
+                        const int cs = __ldg(s.ind + (((Z >> s.lgB) * s.G + (Y >> s.lgB)) * s.G + (X >> s.lgB)));
+                        if (cs < 0) continue;
+                        const int loc = (((Z & (B - 1)) * B) + (Y & (B - 1))) * B + (X & (B - 1));
+                        float* gp = grad_atlas + ((size_t)cs * B3 + loc) * 8;
+                        const float w = wk * tw[c];
+                        atomicAdd(reinterpret_cast<float4*>(gp),
+                                  make_float4(0.0f, w * gfeat[0], w * gfeat[1], w * gfeat[2]));
+                        atomicAdd(reinterpret_cast<float4*>(gp + 4),
+                                  make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
+                    }
+                }
+                if (st.tau > s.taumax) return;
+            }
+        }
+        k = kx;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// view-dependence MLP (Eq. 7): x = [C_d, V, d, sin/cos(2^l d), l = 0..3] -> 16 ReLU ->
+// 16 ReLU -> 3 -> sigmoid. Weights W come from shared memory (uniform broadcast reads).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void mlp_input(const float cd[3], const float v[4], const float d[3], float x[kMlpIn]) {
+    x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
+    x[3] = v[0]; x[4] = v[1]; x[5] = v[2]; x[6] = v[3];
+    x[7] = d[0]; x[8] = d[1]; x[9] = d[2];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float sv, cv;
+            sincosf((float)(1 << l) * d[i], &sv, &cv);
+            x[10 + 6 * l + i] = sv;
+            x[13 + 6 * l + i] = cv;
+        }
+    }
+}
+
+struct MlpAct {
+    float h1[kMlpH], h2[kMlpH], res[kMlpOut];
+};
+
+__device__ __forceinline__ void mlp_forward(const float* W, const float x[kMlpIn], MlpAct& a) {
+#pragma unroll
+    for (int o = 0; o < kMlpH; ++o) {
+        float acc = W[kOffB1 + o];
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) acc = fmaf(W[kOffW1 + o * kMlpIn + i], x[i], acc);
+        a.h1[o] = fmaxf(acc, 0.0f);
+    }
+#pragma unroll
+    for (int o = 0; o < kMlpH; ++o) {
+        float acc = W[kOffB2 + o];
+#pragma unroll
+        for (int i = 0; i < kMlpH; ++i) acc = fmaf(W[kOffW2 + o * kMlpH + i], a.h1[i], acc);
+        a.h2[o] = fmaxf(acc, 0.0f);
+    }
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) {
+        float acc = W[kOffB3 + o];
+#pragma unroll
+        for (int i = 0; i < kMlpH; ++i) acc = fmaf(W[kOffW3 + o * kMlpH + i], a.h2[i], acc);
+        a.res[o] = 1.0f / (1.0f + expf(-acc));
+    }
+}
+
+__device__ __forceinline__ void load_mlp_smem(float* sW, const float* mlp) {
+    for (int i = threadIdx.x + threadIdx.y * blockDim.x; i < kNParam; i += blockDim.x * blockDim.y)
+        sW[i] = __ldg(mlp + i);
+}
+
+// Finish one ray: colour = C_d + residual + T bg (residual only if something was composited).
+__device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, const Ray& r, const MarchState& st,
+                                           float rgb[3], float aux[kAuxCh]) {
+    const float inv255 = 1.0f / 255.0f;
+    float cd[3], v[4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cd[c] = st.acc[c] * inv255;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = st.acc[3 + c] * inv255;
+    float res[3] = {0.0f, 0.0f, 0.0f};
+    if (st.active > 0) {
+        float x[kMlpIn];
+        mlp_input(cd, v, r.d, x);
+        MlpAct a;
+        mlp_forward(sW, x, a);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res[c] = cd[c] + a.res[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rgb[c] = res[c] + st.T * s.bg[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) aux[c] = cd[c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) aux[3 + c] = v[c];
+    aux[7] = 1.0f - st.T;
+}
+
+__device__ __forceinline__ void record_status(const DevScene& s, const MarchState& st) {
+    if (st.limit) atomicCAS(s.status, 0, kStatusStepLimit);
+}
+
+// ---------------------------------------------------------------------------------
+// host-side launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------------
+struct DebugOut {
+    float* aux;
+    int32_t* counts;
+    uint64_t* trace;
+    int32_t trace_cap;
+};
+
+cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, float* rgb,
+                                const DebugOut& dbg, cudaStream_t st);
+cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
+                               int64_t n, const float* mlp, float* rgb, const DebugOut& dbg, cudaStream_t st);
+cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
+                                 const float* mlp, const float* grad_rgb, float* grad_atlas, float* grad_mlp,
+                                 cudaStream_t st);
+cudaError_t launch_validate(const int32_t* ind, int64_t n_ind, int64_t nb, int32_t* blk_of_slot, int32_t* err,
+                            cudaStream_t st);
+cudaError_t launch_build_padded(const int32_t* ind, const int32_t* blk_of_slot, const uint8_t* atlas, int64_t nb,
+                                int N, int B, int lgB, uint8_t* pdens, uint2* patlas, cudaStream_t st);
+
+struct PersistentParams {
+    snerg_camera cams[kMaxCams];
+    int32_t tile_start[kMaxCams + 1];   // prefix sum of work items per camera
+    int32_t tiles_x[kMaxCams];
+    int32_t n_cams;
+    int32_t total_items;
+    int32_t tile_w, tile_h;             // pixels per work item (tile_w * tile_h % 32 == 0)
+    int32_t warp_w, warp_h;             // pixels per warp pass (warp_w * warp_h == 32)
+};
+
+cudaError_t launch_render_persistent(const DevScene& s, const PersistentParams& p, const float* mlp, float* rgb,
+                                     int32_t* queue, int grid, int block, cudaStream_t st);
+const void* persistent_kernel_fn();
+
+}  // namespace snerg

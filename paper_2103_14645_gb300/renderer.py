@@ -1,0 +1,276 @@
+"""Python binding of libsnerg.so (include/snerg.h): argument marshalling only.
+
+Every step of the render and its adjoint runs in the library's CUDA kernels; PyTorch
+supplies device memory and the current stream. There is no fallback: if the library is
+missing or the device is not a CUDA GPU, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsnerg.so")
+MLP_PARAMS = 883
+MAX_CAMERAS = 256
+AUX_CH = 8
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error",
+          4: "a ray exceeded its iteration cap", 5: "unsupported"}
+
+EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_render_rays",
+            "snerg_render_backward", "snerg_last_status", "snerg_launch_count",
+            "snerg_persistent_config", "snerg_destroy", "snerg_status_str"]
+
+
+class SnergError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("B", ctypes.c_int32), ("bmin", ctypes.c_float * 3),
+                ("extent", ctypes.c_float), ("sigma_max", ctypes.c_float), ("bg", ctypes.c_float * 3)]
+
+
+class RenderOpts(ctypes.Structure):
+    _fields_ = [("d_aux", ctypes.c_void_p), ("d_counts", ctypes.c_void_p), ("d_trace", ctypes.c_void_p),
+                ("trace_cap", ctypes.c_int32), ("persistent", ctypes.c_int32), ("tile_w", ctypes.c_int32),
+                ("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+_LIB = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsnerg.so (raises if it has not been built: there is no CPU path)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2103_14645_gb300.build.build() "
+                           "(the renderer has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.snerg_workspace_bytes.argtypes = [P, i64]
+    lib.snerg_workspace_bytes.restype = ctypes.c_size_t
+    lib.snerg_create.argtypes = [P, P, P, i64, P, ctypes.c_size_t, P, P]
+    lib.snerg_create.restype = ctypes.c_int
+    lib.snerg_render.argtypes = [P, P, i32, P, P, P, P]
+    lib.snerg_render.restype = ctypes.c_int
+    lib.snerg_render_rays.argtypes = [P, P, i32, P, i64, P, P, P, P]
+    lib.snerg_render_rays.restype = ctypes.c_int
+    lib.snerg_render_backward.argtypes = [P, P, i32, P, i64, P, P, P, P, P]
+    lib.snerg_render_backward.restype = ctypes.c_int
+    lib.snerg_last_status.argtypes = [P, P]
+    lib.snerg_last_status.restype = ctypes.c_int
+    lib.snerg_launch_count.argtypes = [P]
+    lib.snerg_launch_count.restype = ctypes.c_int64
+    lib.snerg_persistent_config.argtypes = [P, P, P, P]
+    lib.snerg_persistent_config.restype = ctypes.c_int
+    lib.snerg_destroy.argtypes = [P]
+    lib.snerg_destroy.restype = None
+    lib.snerg_status_str.argtypes = [ctypes.c_int]
+    lib.snerg_status_str.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise SnergError(code, where)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _cams(cams) -> np.ndarray:
+    c = np.ascontiguousarray(cams, dtype=synth.CAMERA_DTYPE).reshape(-1)
+    if not 1 <= c.shape[0] <= MAX_CAMERAS:
+        raise ValueError(f"1..{MAX_CAMERAS} cameras per call, got {c.shape[0]}")
+    return c
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor")
+
+
+class Renderer:
+    """A baked SNeRG scene resident on one GPU (snerg_create) and its render calls."""
+
+    def __init__(self, N: int, B: int, bmin, extent: float, sigma_max: float, bg,
+                 indirection: torch.Tensor, atlas: torch.Tensor):
+        self.lib = load_library()
+        _require_cuda(indirection, "indirection", torch.int32)
+        _require_cuda(atlas, "atlas", torch.uint8)
+        self.device = atlas.device if atlas.numel() else indirection.device
+        self.N, self.B = int(N), int(B)
+        self.nb = int(atlas.shape[0]) if atlas.dim() > 0 else 0
+        self.desc = SceneDesc(self.N, self.B, (ctypes.c_float * 3)(*bmin), float(extent),
+                              float(sigma_max), (ctypes.c_float * 3)(*bg))
+        nbytes = self.lib.snerg_workspace_bytes(ctypes.byref(self.desc), self.nb)
+        if nbytes == 0:
+            raise ValueError("invalid scene description")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            code = self.lib.snerg_create(ctypes.byref(self.desc), _ptr(indirection), _ptr(atlas), self.nb,
+                                         _ptr(self.workspace), nbytes, _stream(self.device), ctypes.byref(h))
+        _check(code, "snerg_create")
+        self.handle = h
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda") -> "Renderer":
+        ind = torch.from_numpy(np.ascontiguousarray(scene.ind, np.int32)).to(device)
+        atl = torch.from_numpy(np.ascontiguousarray(scene.atlas, np.uint8)).to(device)
+        return cls(scene.N, scene.B, scene.bmin, scene.extent, scene.sigma_max, scene.bg, ind, atl)
+
+    # ---------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.snerg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.snerg_launch_count(self.handle))
+
+    def persistent_config(self):
+        tw, th, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.snerg_persistent_config(self.handle, ctypes.byref(tw), ctypes.byref(th), ctypes.byref(c)),
+               "snerg_persistent_config")
+        return tw.value, th.value, c.value
+
+    def check_status(self):
+        """Synchronise and raise if a kernel recorded a device-side error."""
+        _check(self.lib.snerg_last_status(self.handle, _stream(self.device)), "device status")
+
+    def _opts(self, n_pix, aux, counts, trace_cap, persistent, tile, ctas_per_sm):
+        out = {}
+        o = RenderOpts()
+        if aux:
+            out["aux"] = torch.empty((n_pix, AUX_CH), dtype=torch.float32, device=self.device)
+            o.d_aux = out["aux"].data_ptr()
+        if counts:
+            out["counts"] = torch.empty((n_pix, 4), dtype=torch.int32, device=self.device)
+            o.d_counts = out["counts"].data_ptr()
+        if trace_cap > 0:
+            out["trace"] = torch.zeros((n_pix, trace_cap), dtype=torch.int64, device=self.device)
+            o.d_trace = out["trace"].data_ptr()
+            o.trace_cap = trace_cap
+        o.persistent = 1 if persistent else 0
+        if tile is not None:
+            o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
+        o.ctas_per_sm = int(ctas_per_sm)
+        return o, out
+
+    def render(self, cams, mlp: torch.Tensor, out: torch.Tensor | None = None, aux=False, counts=False,
+               trace_cap: int = 0, persistent=False, tile=None, ctas_per_sm: int = 0):
+        """Render every pixel of the cameras into out [pixels, 3] (packed by out_offset).
+        Returns out, or a dict with 'rgb' and the requested debug outputs."""
+        c = _cams(cams)
+        _require_cuda(mlp, "mlp", torch.float32)
+        n_pix = int(max((int(x["out_offset"]) + int(x["W"]) * int(x["H"]) for x in c), default=0))
+        if out is None:
+            out = torch.empty((n_pix, 3), dtype=torch.float32, device=self.device)
+        else:
+            _require_cuda(out, "out", torch.float32)
+            if out.numel() < 3 * n_pix:
+                raise ValueError("out is too small")
+        o, extra = self._opts(n_pix, aux, counts, trace_cap, persistent, tile, ctas_per_sm)
+        code = self.lib.snerg_render(self.handle, c.ctypes.data, c.shape[0], _ptr(mlp), _ptr(out),
+                                     ctypes.byref(o), _stream(self.device))
+        _check(code, "snerg_render")
+        if extra:
+            extra["rgb"] = out
+            return extra
+        return out
+
+    def render_rays(self, cams, pix: torch.Tensor, mlp: torch.Tensor, out=None, aux=False, counts=False,
+                    trace_cap: int = 0):
+        c = _cams(cams)
+        _require_cuda(pix, "pix", torch.int32)
+        _require_cuda(mlp, "mlp", torch.float32)
+        n = int(pix.shape[0])
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=self.device)
+        o, extra = self._opts(n, aux, counts, trace_cap, False, None, 0)
+        code = self.lib.snerg_render_rays(self.handle, c.ctypes.data, c.shape[0], _ptr(pix), n, _ptr(mlp),
+                                          _ptr(out), ctypes.byref(o), _stream(self.device))
+        _check(code, "snerg_render_rays")
+        if extra:
+            extra["rgb"] = out
+            return extra
+        return out
+
+    def backward(self, cams, pix: torch.Tensor, mlp: torch.Tensor, grad_rgb: torch.Tensor,
+                 grad_atlas: torch.Tensor | None = None, grad_mlp: torch.Tensor | None = None):
+        """Accumulate dL/d(atlas values) [nb,B,B,B,8] and dL/d(mlp) [883] for dL/dC."""
+        c = _cams(cams)
+        _require_cuda(pix, "pix", torch.int32)
+        _require_cuda(mlp, "mlp", torch.float32)
+        _require_cuda(grad_rgb, "grad_rgb", torch.float32)
+        if grad_atlas is not None:
+            _require_cuda(grad_atlas, "grad_atlas", torch.float32)
+            if grad_atlas.numel() != self.nb * self.B ** 3 * 8:
+                raise ValueError("grad_atlas must have nb*B^3*8 elements")
+        if grad_mlp is not None:
+            _require_cuda(grad_mlp, "grad_mlp", torch.float32)
+        code = self.lib.snerg_render_backward(self.handle, c.ctypes.data, c.shape[0], _ptr(pix), int(pix.shape[0]),
+                                              _ptr(mlp), _ptr(grad_rgb), _ptr(grad_atlas), _ptr(grad_mlp),
+                                              _stream(self.device))
+        _check(code, "snerg_render_backward")
+
+
+class SnergRenderFn(torch.autograd.Function):
+    """C(rays) with gradients to the MLP weights and to the decoded atlas values.
+
+    `atlas_values` stands for the decoded colour/feature values q/255 (shape
+    [nb, B, B, B, 8]) of the atlas the renderer was created with; the forward pass reads
+    the uint8 atlas inside the renderer, and backward returns dL/d(atlas_values) with the
+    density channel (0) frozen at zero."""
+
+    @staticmethod
+    def forward(ctx, mlp, atlas_values, renderer, cams, pix):
+        ctx.renderer = renderer
+        ctx.cams = cams
+        ctx.save_for_backward(mlp, pix)
+        ctx.atlas_shape = atlas_values.shape
+        ctx.want_atlas = atlas_values.requires_grad
+        return renderer.render_rays(cams, pix, mlp.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_rgb):
+        mlp, pix = ctx.saved_tensors
+        r = ctx.renderer
+        g_mlp = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=r.device) if ctx.needs_input_grad[0] else None
+        g_atl = (torch.zeros(ctx.atlas_shape, dtype=torch.float32, device=r.device)
+                 if ctx.needs_input_grad[1] else None)
+        if g_mlp is not None or g_atl is not None:
+            r.backward(ctx.cams, pix, mlp.detach().contiguous(), grad_rgb.contiguous().float(), g_atl, g_mlp)
+        return g_mlp, g_atl, None, None, None
+
+
+def render_rays_autograd(renderer: Renderer, cams, pix: torch.Tensor, mlp: torch.Tensor,
+                         atlas_values: torch.Tensor) -> torch.Tensor:
+    return SnergRenderFn.apply(mlp, atlas_values, renderer, cams, pix)

@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA renderer (through the C ABI) against the FP64 oracle.
+
+Bar: step counts, composited-sample counts and visited-voxel traces bit-exact; colours
+and the auxiliary composites (C_d, V, opacity) within 1e-4 absolute; gradients within
+1e-4 of the largest oracle gradient entry (FP32 accumulation of many terms vs FP64).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2103_14645_gb300 import renderer, synth
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+DEV = torch.device("cuda:0")
+
+_SCENES = {}
+
+
+def scene(name):
+    if name not in _SCENES:
+        _SCENES[name] = synth.make_scene(name)
+    return _SCENES[name]
+
+
+def gpu_render(sc, cams=None, mlp=None, **kw):
+    r = renderer.Renderer.from_scene(sc, DEV)
+    w = torch.from_numpy(np.asarray(sc.mlp if mlp is None else mlp, np.float32)).to(DEV)
+    out = r.render(sc.cameras if cams is None else cams, w, **kw)
+    r.check_status()
+    if isinstance(out, dict):
+        return {k: v.cpu().numpy() for k, v in out.items()}, r
+    return {"rgb": out.cpu().numpy()}, r
+
+
+def oracle_all(sc, cams=None, mlp=None, trace_cap=0):
+    cams = sc.cameras if cams is None else cams
+    pix = synth.all_pixels(cams)
+    return oracle.render_rays(sc, pix, mlp=mlp, cams=cams, trace_cap=trace_cap)
+
+
+def assert_parity(g, o, trace=True):
+    np.testing.assert_array_equal(g["counts"][:, :2], o["counts"])
+    assert (g["counts"][:, 2] >= (g["counts"][:, 0] > 0)).all()
+    if trace and "trace" in g:
+        np.testing.assert_array_equal(g["trace"].astype(np.uint64), o["trace"])
+    assert np.abs(g["rgb"] - o["rgb"]).max() <= TOL
+    assert np.abs(g["aux"] - o["aux"]).max() <= TOL
+
+
+@pytest.mark.parametrize("name", ["tiny", "gauss64"])
+def test_forward_parity_full_image(name):
+    sc = scene(name)
+    g, _ = gpu_render(sc, aux=True, counts=True, trace_cap=64)
+    o = oracle_all(sc, trace_cap=64)
+    assert o["counts"][:, 1].max() <= 64
+    assert_parity(g, o)
+    assert (o["counts"][:, 1] > 0).mean() > 0.2
+
+
+def test_forward_parity_ragged_and_multi_camera():
+    """Image sizes that are not multiples of the 16x8 CTA tile, several cameras packed."""
+    sc = scene("gauss64")
+    cams = synth.orbit_cameras(np.random.default_rng(4), [(37, 23), (1, 1), (64, 9), (5, 70)], synth.CAM_RADIUS)
+    g, _ = gpu_render(sc, cams=cams, aux=True, counts=True, trace_cap=64)
+    o = oracle_all(sc, cams=cams, trace_cap=64)
+    assert_parity(g, o)
+
+
+def test_forward_parity_paper_scale_view():
+    """1024^3 grid, 32^3 blocks, one 800x800 view: the benchmarked launch. Every pixel's
+    colour and counts are compared; visited voxels on 4096 sampled rays."""
+    sc = scene("shell1024")
+    g, r = gpu_render(sc, counts=True, aux=True)
+    o = oracle_all(sc)
+    np.testing.assert_array_equal(g["counts"][:, :2], o["counts"])
+    assert np.abs(g["rgb"] - o["rgb"]).max() <= TOL
+    assert np.abs(g["aux"] - o["aux"]).max() <= TOL
+    pix = synth.random_pixels(np.random.default_rng(7), sc.cameras, 4096)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    gt = r.render_rays(sc.cameras, torch.from_numpy(pix).to(DEV), w, counts=True, trace_cap=64)
+    r.check_status()
+    ot = oracle.render_rays(sc, pix, trace_cap=64)
+    assert ot["counts"][:, 1].max() <= 64
+    np.testing.assert_array_equal(gt["trace"].cpu().numpy().astype(np.uint64), ot["trace"])
+    np.testing.assert_array_equal(gt["counts"].cpu().numpy()[:, :2], ot["counts"])
+
+
+def test_rays_path_equals_image_path():
+    sc = scene("gauss64")
+    g, r = gpu_render(sc)
+    pix = synth.all_pixels(sc.cameras)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    rr = r.render_rays(sc.cameras, torch.from_numpy(pix).to(DEV), w).cpu().numpy()
+    np.testing.assert_array_equal(rr, g["rgb"])
+
+
+@pytest.mark.parametrize("tile", [None, (8, 4), (4, 8), (16, 2), (32, 1), (8, 16)])
+def test_persistent_equals_plain(tile):
+    """One persistent graph launch over several cameras of uneven sizes renders exactly
+    what one launch per camera renders."""
+    sc = scene("gauss64")
+    cams = synth.orbit_cameras(np.random.default_rng(8), [(64, 64), (37, 23), (200, 120), (8, 8), (0, 5), (90, 31)],
+                               synth.CAM_RADIUS)
+    plain, _ = gpu_render(sc, cams=cams)
+    r = renderer.Renderer.from_scene(sc, DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    kw = {} if tile is None else {"tile": tile, "ctas_per_sm": 2}
+    for _ in range(2):   # first call captures (and may autotune), second replays the graph
+        out = r.render(cams, w, persistent=True, **kw).cpu().numpy()
+        r.check_status()
+        np.testing.assert_array_equal(out, plain["rgb"])
+    tw, th, c = r.persistent_config()
+    assert tw * th % 32 == 0 and c > 0
+
+
+def test_persistent_replay_with_new_poses():
+    sc = scene("gauss64")
+    r = renderer.Renderer.from_scene(sc, DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    for seed in range(3):
+        cams = synth.orbit_cameras(np.random.default_rng(100 + seed), [(48, 40)] * 5, synth.CAM_RADIUS)
+        out = r.render(cams, w, persistent=True, tile=(8, 4), ctas_per_sm=4).cpu().numpy()
+        plain = r.render(cams, w).cpu().numpy()
+        np.testing.assert_array_equal(out, plain)
+
+
+def test_max_camera_count():
+    sc = scene("tiny")
+    cams = synth.orbit_cameras(np.random.default_rng(9), [(7, 5)] * renderer.MAX_CAMERAS, synth.CAM_RADIUS)
+    g, _ = gpu_render(sc, cams=cams, counts=True)
+    o = oracle_all(sc, cams=cams)
+    np.testing.assert_array_equal(g["counts"][:, :2], o["counts"])
+    assert np.abs(g["rgb"] - o["rgb"]).max() <= TOL
+    p, _ = gpu_render(sc, cams=cams, persistent=True, tile=(8, 4), ctas_per_sm=2)
+    np.testing.assert_array_equal(p["rgb"], g["rgb"])
+
+
+# --------------------------------------------------------------------------------------
+# closed forms and degenerate cases on the GPU
+# --------------------------------------------------------------------------------------
+
+def test_gpu_uniform_slab_closed_form():
+    import math
+    col = np.array([100, 150, 200, 10, 20, 30, 40])
+    sc = helpers.slab_scene(z_range=(4, 6), q=200, color=col, sigma_max_vox=1.0)
+    g, _ = gpu_render(sc, aux=True, counts=True, trace_cap=4)
+    T = math.exp(-2 * 200 / 255.0)
+    assert g["counts"][0, :2].tolist() == [4, 2]
+    np.testing.assert_allclose(g["aux"][0, 7], 1 - T, atol=1e-6)
+    np.testing.assert_allclose(g["rgb"][0], col[:3] / 255.0 * (1 - T) + T, atol=1e-6)
+
+
+def test_gpu_early_exit_count():
+    sc = helpers.slab_scene(z_range=(2, 14), q=255, sigma_max_vox=1.0)
+    g, _ = gpu_render(sc, counts=True)
+    assert g["counts"][0, :2].tolist() == [9, 7]
+
+
+def test_gpu_empty_grid_is_background():
+    sc0 = scene("tiny")
+    sc = synth.custom_scene(sc0.N, sc0.B, np.full_like(sc0.ind, -1), np.zeros((0, sc0.B, sc0.B, sc0.B, 8), np.uint8),
+                            sc0.sigma_max, sc0.mlp, sc0.cameras)
+    g, _ = gpu_render(sc, counts=True)
+    assert (g["rgb"] == np.asarray(sc.bg, np.float32)).all()
+    assert (g["counts"] == 0).all()
+
+
+def test_gpu_camera_inside_grid_and_axis_rays():
+    """Camera inside the grid (t_start = 0), principal rays parallel to the axes (zero
+    direction components), origins on voxel faces."""
+    sc = scene("gauss64")
+    cams = np.concatenate([
+        helpers.axis_camera((0.0, 0.0, 0.0), W=9, H=7, f=4.0),
+        helpers.axis_camera((0.25, -0.5, 1.5), W=1, H=1),
+        helpers.axis_camera((0.03125, 0.0625, 1.2), W=3, H=3, f=1e6),
+    ])
+    cams["out_offset"] = [0, 63, 64]
+    g, _ = gpu_render(sc, cams=cams, aux=True, counts=True, trace_cap=64)
+    o = oracle_all(sc, cams=cams, trace_cap=64)
+    assert_parity(g, o)
+    assert o["counts"][:, 1].sum() > 0
+
+
+def test_gpu_zero_weight_mlp():
+    sc = scene("tiny")
+    w0 = np.zeros(synth.MLP_NPARAM, np.float32)
+    g, _ = gpu_render(sc, mlp=w0, aux=True, counts=True)
+    act = g["counts"][:, 1] > 0
+    T = 1 - g["aux"][:, 7]
+    np.testing.assert_allclose(g["rgb"][act], g["aux"][act, :3] + 0.5 + T[act, None], atol=1e-6)
+    assert (g["rgb"][~act] == 1.0).all()
+
+
+def test_gpu_invalid_inputs_raise():
+    sc = scene("tiny")
+    ind = torch.from_numpy(sc.ind).to(DEV)
+    atl = torch.from_numpy(sc.atlas).to(DEV)
+    args = (sc.N, sc.B, sc.bmin, sc.extent, sc.sigma_max, sc.bg)
+    bad = sc.ind.copy()
+    bad.flat[np.nonzero(sc.ind.ravel() >= 0)[0][0]] = sc.nb
+    with pytest.raises(renderer.SnergError) as e:
+        renderer.Renderer(*args, torch.from_numpy(bad).to(DEV), atl)
+    assert e.value.code == 1
+    dup = sc.ind.copy()
+    occ = np.nonzero(dup.ravel() >= 0)[0]
+    dup.flat[occ[1]] = dup.flat[occ[0]]
+    with pytest.raises(renderer.SnergError):
+        renderer.Renderer(*args, torch.from_numpy(dup).to(DEV), atl)
+    with pytest.raises(renderer.SnergError):
+        renderer.Renderer(sc.N, 3, sc.bmin, sc.extent, sc.sigma_max, sc.bg, ind, atl)
+    r = renderer.Renderer(*args, ind, atl)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    cams = sc.cameras.copy()
+    cams[0]["fx"] = np.nan
+    with pytest.raises(renderer.SnergError):
+        r.render(cams, w)
+    pix = torch.tensor([[0, 0, 0], [1, 0, 0], [0, 10 ** 6, 0]], dtype=torch.int32, device=DEV)
+    r.render_rays(sc.cameras, pix, w)
+    with pytest.raises(renderer.SnergError) as e:
+        r.check_status()
+    assert e.value.code == 1
+    r.check_status()       # the status word was cleared by the previous read
+    out = r.render_rays(sc.cameras, torch.zeros((0, 3), dtype=torch.int32, device=DEV), w)
+    assert out.shape == (0, 3)
+
+
+# --------------------------------------------------------------------------------------
+# backward
+# --------------------------------------------------------------------------------------
+
+def _bwd_case(sc, n, seed):
+    rng = np.random.default_rng(seed)
+    pix = synth.random_pixels(rng, sc.cameras, n)
+    g = rng.normal(size=(n, 3)).astype(np.float32)
+    return pix, g
+
+
+def gpu_backward(sc, pix, g, mlp=None):
+    r = renderer.Renderer.from_scene(sc, DEV)
+    w = torch.from_numpy(np.asarray(sc.mlp if mlp is None else mlp, np.float32)).to(DEV)
+    ga = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=DEV)
+    gm = torch.zeros(883, dtype=torch.float32, device=DEV)
+    r.backward(sc.cameras, torch.from_numpy(pix).to(DEV), w, torch.from_numpy(g).to(DEV), ga, gm)
+    r.check_status()
+    return ga.cpu().numpy(), gm.cpu().numpy(), r
+
+
+@pytest.mark.parametrize("name,n", [("tiny", 480), ("gauss64", 4096), ("bwd512", 65536)])
+def test_backward_matches_oracle_gradient(name, n):
+    sc = scene(name)
+    pix, g = _bwd_case(sc, n, 31)
+    ga, gm, _ = gpu_backward(sc, pix, g)
+    ra, rm = oracle.backward_rays(sc, pix, g)
+    assert (ga[..., 0] == 0).all()
+    sa = np.abs(ra).max()
+    sm = np.abs(rm).max()
+    assert sa > 0 and sm > 0
+    assert np.abs(ga - ra).max() <= 1e-4 * sa
+    assert np.abs(gm - rm).max() <= 1e-4 * sm
+
+
+def test_backward_mlp_central_differences():
+    """GPU gradient w.r.t. 64 sampled MLP weights vs central differences (h = 1e-3) of
+    the GPU forward, L = 1/2 sum |C - target|^2 over 4096 rays of the 512^3 scene."""
+    sc = scene("bwd512")
+    n = 4096
+    pix = sc.extra["pix"][:n]
+    target = sc.extra["target"][:n]
+    r = renderer.Renderer.from_scene(sc, DEV)
+    pt = torch.from_numpy(pix).to(DEV)
+    w0 = torch.from_numpy(sc.mlp).to(DEV)
+
+    def loss(w):
+        c = r.render_rays(sc.cameras, pt, w).double().cpu().numpy()
+        return 0.5 * ((c - target) ** 2).sum(), c
+
+    L0, c0 = loss(w0)
+    gm = torch.zeros(883, dtype=torch.float32, device=DEV)
+    r.backward(sc.cameras, pt, w0, torch.from_numpy((c0 - target).astype(np.float32)).to(DEV), None, gm)
+    r.check_status()
+    gm = gm.cpu().numpy()
+    h = 1e-3
+    picks = np.random.default_rng(5).choice(883, 64, replace=False)
+    scale = np.abs(gm).max()
+    for p in picks:
+        wp, wm = w0.clone(), w0.clone()
+        wp[p] += h
+        wm[p] -= h
+        fd = (loss(wp)[0] - loss(wm)[0]) / (2 * h)
+        assert abs(fd - gm[p]) <= 2e-2 * abs(fd) + 1e-3 * scale, (p, fd, gm[p])
+
+
+def test_backward_atlas_code_differences():
+    """GPU gradient w.r.t. 64 sampled colour/feature values vs central differences of
+    the GPU forward with the uint8 code moved by +-1 (h = 1/255)."""
+    sc = scene("gauss64")
+    n = 4096
+    pix, _ = _bwd_case(sc, n, 3)
+    target = np.random.default_rng(4).uniform(size=(n, 3))
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    pt = torch.from_numpy(pix).to(DEV)
+
+    def loss(atlas):
+        s2 = synth.custom_scene(sc.N, sc.B, sc.ind, atlas, sc.sigma_max, sc.mlp, sc.cameras)
+        r = renderer.Renderer.from_scene(s2, DEV)
+        c = r.render_rays(sc.cameras, pt, w).double().cpu().numpy()
+        return 0.5 * ((c - target) ** 2).sum(), c
+
+    L0, c0 = loss(sc.atlas)
+    ga, _, _ = gpu_backward(sc, pix, (c0 - target).astype(np.float32))
+    flat = ga.reshape(-1)
+    atl = sc.atlas.reshape(-1)
+    cand = np.nonzero((np.abs(flat) > 1e-3 * np.abs(flat).max()) & (np.arange(flat.size) % 8 != 0)
+                      & (atl > 0) & (atl < 255))[0]
+    picks = np.random.default_rng(6).choice(cand, 64, replace=False)
+    h = 1.0 / 255.0
+    for idx in picks:
+        ap, am = sc.atlas.copy().reshape(-1), sc.atlas.copy().reshape(-1)
+        ap[idx] += 1
+        am[idx] -= 1
+        fd = (loss(ap.reshape(sc.atlas.shape))[0] - loss(am.reshape(sc.atlas.shape))[0]) / (2 * h)
+        assert abs(fd - flat[idx]) <= 2e-2 * abs(fd) + 1e-3 * np.abs(flat).max(), (idx, fd, flat[idx])
+
+
+def test_autograd_function():
+    sc = scene("gauss64")
+    pix, _ = _bwd_case(sc, 2048, 8)
+    r = renderer.Renderer.from_scene(sc, DEV)
+    pt = torch.from_numpy(pix).to(DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV).requires_grad_(True)
+    vals = (torch.from_numpy(sc.atlas).to(DEV).float() / 255.0).requires_grad_(True)
+    target = torch.rand((2048, 3), device=DEV, generator=torch.Generator(DEV).manual_seed(0))
+    c = renderer.render_rays_autograd(r, sc.cameras, pt, w, vals)
+    loss = 0.5 * ((c - target) ** 2).sum()
+    loss.backward()
+    ga, gm, _ = gpu_backward(sc, pix, (c.detach() - target).cpu().numpy())
+    np.testing.assert_allclose(w.grad.cpu().numpy(), gm, rtol=0, atol=1e-5 * np.abs(gm).max())
+    np.testing.assert_allclose(vals.grad.cpu().numpy(), ga, rtol=0, atol=1e-5 * np.abs(ga).max())

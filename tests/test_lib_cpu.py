@@ -1,0 +1,107 @@
+"""Host-side checks of the C ABI library that need no GPU: it builds, loads, exports
+every entry point include/snerg.h declares, sizes workspaces, and rejects invalid
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2103_14645_gb300 import build, renderer, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "snerg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if build.sources_newer_than_lib():
+        build.build()
+    return renderer.load_library()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(snerg_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["snerg_create", "snerg_render", "snerg_render_rays", "snerg_render_backward", "snerg_destroy",
+              "snerg_workspace_bytes", "snerg_last_status", "snerg_status_str"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(renderer.EXPORTED) == names
+
+
+def test_nm_shows_c_linkage(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", renderer.LIB_PATH], capture_output=True, text=True).stdout
+    for n in declared_functions():
+        assert re.search(rf"\bT {n}$", out, flags=re.M), n
+
+
+def _desc(N=64, B=8, extent=2.0, sigma=10.0):
+    return renderer.SceneDesc(N, B, (ctypes.c_float * 3)(-1, -1, -1), extent, sigma, (ctypes.c_float * 3)(1, 1, 1))
+
+
+def test_workspace_bytes(lib):
+    for N, B, nb in [(64, 8, 155), (1024, 32, 1900), (16, 4, 0), (2048, 32, 6281)]:
+        d = _desc(N, B)
+        got = lib.snerg_workspace_bytes(ctypes.byref(d), nb)
+        G, P = N // B, B + 2
+        need = 4 * G ** 3 + 4 * nb + 9 * nb * P ** 3
+        assert need <= got <= need + 5 * 256 + 256
+        assert got % 256 == 0
+    for bad in [_desc(64, 6), _desc(60, 8), _desc(64, 8, extent=0.0), _desc(64, 8, sigma=float("nan")),
+                _desc(0, 8), _desc(64 * 1024, 8), _desc(8192, 4)]:
+        assert lib.snerg_workspace_bytes(ctypes.byref(bad), 10) == 0
+    assert lib.snerg_workspace_bytes(ctypes.byref(_desc()), -1) == 0
+    assert lib.snerg_workspace_bytes(None, 1) == 0
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    h = ctypes.c_void_p(123)
+    d = _desc()
+    assert lib.snerg_create(ctypes.byref(d), None, None, 0, None, 0, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    bad = _desc(64, 6)
+    assert lib.snerg_create(ctypes.byref(bad), 1, 1, 0, 256, 1 << 20, None, ctypes.byref(h)) == 1
+    # workspace too small / misaligned
+    assert lib.snerg_create(ctypes.byref(d), 256, 256, 1, 256, 16, None, ctypes.byref(h)) == 2
+    assert lib.snerg_create(ctypes.byref(d), 256, 256, 1, 257, 1 << 30, None, ctypes.byref(h)) == 1
+    cams = np.zeros(1, synth.CAMERA_DTYPE)
+    assert lib.snerg_render(None, cams.ctypes.data, 1, None, None, None, None) == 1
+    assert lib.snerg_render_rays(None, cams.ctypes.data, 1, None, 0, None, None, None, None) == 1
+    assert lib.snerg_render_backward(None, cams.ctypes.data, 1, None, 0, None, None, None, None, None) == 1
+    assert lib.snerg_last_status(None, None) == 1
+    assert lib.snerg_launch_count(None) == 0
+    lib.snerg_destroy(None)
+
+
+def test_status_strings(lib):
+    for code, text in renderer.STATUS.items():
+        assert lib.snerg_status_str(code).decode() == text
+    assert lib.snerg_status_str(99).decode() == "unknown status"
+
+
+def test_camera_record_layout():
+    """The numpy camera dtype matches snerg_camera (80 bytes, out_offset at byte 72)."""
+    assert synth.CAMERA_DTYPE.itemsize == 80
+    assert synth.CAMERA_DTYPE.fields["out_offset"][1] == 72
+    assert synth.CAMERA_DTYPE.fields["W"][1] == 64
+    assert ctypes.sizeof(renderer.RenderOpts) == 48
+
+
+def test_no_cpu_fallback_without_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(renderer, "_LIB", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        renderer.load_library(str(tmp_path / "missing.so"))

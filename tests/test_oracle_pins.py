@@ -212,7 +212,8 @@ def _brute_force_ray(scene, dense, mlp, cam, px, py):
     dens = dense[..., 0].astype(np.float64)
     chans = [dense[..., c].astype(np.float64) / 255.0 for c in range(1, 8)]
     occ = scene.ind >= 0
-    delta = scene.extent / N
+    delta = float(np.float32(scene.extent)) / N
+    sigma_max = float(np.float32(scene.sigma_max))     # the scene description is binary32
     T, feat, steps, visited, tau = 1.0, np.zeros(7), 0, [], 0.0
     k = 0
     while hit:
@@ -230,7 +231,7 @@ def _brute_force_ray(scene, dense, mlp, cam, px, py):
         visited.append(int((j[2] * N + j[1]) * N + j[0]))
         coord = (np.asarray(u[::-1], np.float64) - 0.5).reshape(3, 1)
         s = map_coordinates(dens, coord, order=1, mode="nearest")[0]
-        sd = s / 255.0 * scene.sigma_max * delta
+        sd = s / 255.0 * sigma_max * delta
         w = T * (1 - math.exp(-sd))
         for c in range(7):
             feat[c] += w * map_coordinates(chans[c], coord, order=1, mode="nearest")[0]
