@@ -26,8 +26,10 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-    size_t ind, blk, pdens, patlas, total;
+    size_t ind, bdist, btmp, blk, vskip, patlas, total;
 };
+
+constexpr int kBlockDistCap = 32;   // block-level distances are capped (a smaller box is still empty)
 
 int ilog2_exact(int v) {
     int l = 0;
@@ -52,10 +54,13 @@ bool make_layout(const snerg_scene_desc* d, int64_t nb, Layout* L) {
     const int64_t G = d->N / d->B;
     const int64_t P = d->B + 2;
     const size_t P3 = (size_t)(P * P * P);
+    const size_t G3 = (size_t)(G * G * G);
     L->ind = kAlign;                                          // [0, 256): header words
-    L->blk = align_up(L->ind + (size_t)(G * G * G) * 4);
-    L->pdens = align_up(L->blk + (size_t)nb * 4);
-    L->patlas = align_up(L->pdens + (size_t)nb * P3);
+    L->bdist = align_up(L->ind + G3 * 4);
+    L->btmp = align_up(L->bdist + G3);                        // 2 G^3 scratch (set-up only)
+    L->blk = align_up(L->btmp + 2 * G3);
+    L->vskip = align_up(L->blk + (size_t)nb * 4);
+    L->patlas = align_up(L->vskip + (size_t)nb * P3);
     L->total = align_up(L->patlas + (size_t)nb * P3 * 8);
     return true;
 }
@@ -106,8 +111,6 @@ struct snerg_scene {
     PersistentConfig last{0, 0, 0, 0, 0};
 };
 
-static snerg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SNERG_OK : SNERG_E_CUDA; }
-
 extern "C" size_t snerg_workspace_bytes(const snerg_scene_desc* desc, int64_t num_blocks) {
     Layout L;
     if (!make_layout(desc, num_blocks, &L)) return 0;
@@ -136,9 +139,15 @@ extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t
     const int N = desc->N, B = desc->B, G = N / B, P = B + 2;
     const int64_t G3 = (int64_t)G * G * G;
     int32_t* ws_ind = (int32_t*)(h->ws + L.ind);
+    uint8_t* bdist = h->ws + L.bdist;
+    uint8_t* btmp = h->ws + L.btmp;
     int32_t* blk = (int32_t*)(h->ws + L.blk);
-    uint8_t* pdens = h->ws + L.pdens;
+    uint8_t* vskip = h->ws + L.vskip;
     uint2* patlas = (uint2*)(h->ws + L.patlas);
+    // the voxel distance transform runs before the padded atlas exists and borrows its
+    // region (8 (B+2)^3 >= 2 B^3 bytes per block) as scratch
+    uint8_t* vtmp0 = (uint8_t*)patlas;
+    uint8_t* vtmp1 = vtmp0 + (size_t)num_blocks * B * B * B;
 
     cudaError_t e = cudaMemsetAsync(h->hdr, 0, kAlign, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ws_ind, d_indirection, (size_t)G3 * 4, cudaMemcpyDeviceToDevice, st);
@@ -149,14 +158,18 @@ extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { delete h; return SNERG_E_CUDA; }
     if (err != 0) { delete h; return SNERG_E_INVAL; }
-    e = launch_build_padded(ws_ind, blk, d_atlas, num_blocks, N, B, ilog2_exact(B), pdens, patlas, st);
+    e = launch_block_distance(ws_ind, G, kBlockDistCap, btmp, btmp + G3, bdist, st);
+    if (e == cudaSuccess) e = launch_voxel_distance(d_atlas, num_blocks, B, vtmp0, vtmp1, vskip, st);
+    if (e == cudaSuccess)
+        e = launch_build_padded(ws_ind, blk, d_atlas, num_blocks, N, B, ilog2_exact(B), patlas, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { delete h; return SNERG_E_CUDA; }
-    h->launches = 2;
+    h->launches = 2 + 4 + (num_blocks > 0 ? 5 : 0);
 
     DevScene& s = h->ds;
     s.ind = ws_ind;
-    s.pdens = pdens;
+    s.bdist = bdist;
+    s.vskip = vskip;
     s.patlas = patlas;
     s.status = h->hdr + kHdrStatus;
     s.N = N;

@@ -15,11 +15,21 @@
 //
 // Device layout (built by snerg_prep.cu inside the caller's workspace):
 //   ind    int32 [G^3]                 indirection, -1 = empty (z, y, x)
-//   pdens  uint8 [nb][P^3], P = B + 2  density codes of each block with a 1-voxel apron
+//   bdist  uint8 [G^3]                 Chebyshev distance (in blocks, capped) from each
+//                                      block to the nearest occupied block; 0 = occupied
+//   vskip  uint8 [nb][P^3], P = B + 2  per interior voxel, Chebyshev distance (in voxels)
+//                                      to the nearest voxel of the same block with a
+//                                      non-zero density code; 0 <=> the voxel's own code
+//                                      is non-zero (this plane is the density probe)
 //   patlas uint2 [nb][P^3]             all 8 channels (density, r, g, b | f0..f3)
 // The apron holds the neighbouring blocks' voxels (0 where the neighbour is empty) and
 // the clamped edge voxel at the grid border, so every trilinear stencil of a sample
 // whose nearest voxel lies in block b reads only block b's padded copy.
+//
+// The two distance maps only let the march skip samples that provably contribute
+// nothing (their nearest voxel is in an empty block, or has a zero density code); the
+// lattice, the visited samples and the counts are exactly those of a sample-by-sample
+// march.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -49,7 +59,8 @@ constexpr int kStatusStepLimit = SNERG_E_STEP_LIMIT;
 
 struct DevScene {
     const int32_t* ind;
-    const uint8_t* pdens;
+    const uint8_t* bdist;
+    const uint8_t* vskip;
     const uint2* patlas;
     int32_t* status;
     int32_t N, B, lgB, G, P, P3;
@@ -134,52 +145,56 @@ __device__ __forceinline__ int nearest_voxel(float u, int N) {
     return min(max((int)floorf(u), 0), N - 1);
 }
 
-// true iff sample k lies before the ray's exit and its nearest voxel is in block b
-__device__ __forceinline__ bool in_block(const DevScene& s, const Ray& r, int k, const int b[3]) {
+// true iff sample k lies before the ray's exit and its nearest voxel's block lies in
+// the box lo..hi (inclusive, per axis)
+__device__ __forceinline__ bool in_box(const DevScene& s, const Ray& r, int k, const int lo[3], const int hi[3]) {
     const float t = lattice_t(r, k);
     if (!(t < r.t1)) return false;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-        if ((nearest_voxel(lattice_u(r, t, i), s.N) >> s.lgB) != b[i]) return false;
+    for (int i = 0; i < 3; ++i) {
+        const int b = nearest_voxel(lattice_u(r, t, i), s.N) >> s.lgB;
+        if (b < lo[i] || b > hi[i]) return false;
+    }
     return true;
 }
 
-// First lattice index k' > k with in_block(k') false. Each axis's nearest voxel is a
-// monotone function of k (every step of the lattice arithmetic is a rounded monotone
-// operation), so the samples of one block form a contiguous run: estimate its end from
-// the ray/box exit distance, then confirm or correct with an exact search.
-__device__ __forceinline__ int block_exit(const DevScene& s, const Ray& r, int k, const int b[3]) {
-    float te = INFINITY;
+// First lattice index k' > k with in_box(k') false, given in_box(k). Each axis's
+// nearest voxel is a monotone function of k (every step of the lattice arithmetic is a
+// rounded monotone operation), so the samples inside a box form one contiguous run:
+// estimate its end from the ray/box exit distance, then confirm or correct it with an
+// exact search on the lattice itself.
+__device__ __forceinline__ int box_exit(const DevScene& s, const Ray& r, const float inv_d[3], int k,
+                                        const int lo[3], const int hi[3]) {
+    float te = r.t1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        if (r.d[i] > 0.0f) te = fminf(te, ((float)((b[i] + 1) << s.lgB) - r.o[i]) / r.d[i]);
-        else if (r.d[i] < 0.0f) te = fminf(te, ((float)(b[i] << s.lgB) - r.o[i]) / r.d[i]);
+        if (r.d[i] > 0.0f) te = fminf(te, ((float)((hi[i] + 1) * s.B) - r.o[i]) * inv_d[i]);
+        else if (r.d[i] < 0.0f) te = fminf(te, ((float)(lo[i] * s.B) - r.o[i]) * inv_d[i]);
     }
-    te = fminf(te, r.t1);
-    float kf = ceilf(te - r.t0 - 0.5f);
-    int ke = (kf > (float)s.kmax) ? s.kmax : (int)kf;
+    const float kf = ceilf(te - r.t0 - 0.5f);
+    int ke = (kf > (float)s.kmax) ? s.kmax : (kf < 0.0f ? 0 : (int)kf);
     ke = max(ke, k + 1);
-    int lo = k, hi;
-    if (ke - 1 > k && !in_block(s, r, ke - 1, b)) {
-        hi = ke - 1;
-    } else if (ke < s.kmax && in_block(s, r, ke, b)) {
-        lo = ke;
+    int lo_k = k, hi_k;
+    if (ke - 1 > k && !in_box(s, r, ke - 1, lo, hi)) {
+        hi_k = ke - 1;
+    } else if (ke < s.kmax && in_box(s, r, ke, lo, hi)) {
+        lo_k = ke;
         int step = 1;
         for (;;) {
-            hi = lo + step;
-            if (hi >= s.kmax) { hi = s.kmax; break; }
-            if (!in_block(s, r, hi, b)) break;
-            lo = hi;
+            hi_k = lo_k + step;
+            if (hi_k >= s.kmax) { hi_k = s.kmax; break; }
+            if (!in_box(s, r, hi_k, lo, hi)) break;
+            lo_k = hi_k;
             step <<= 1;
         }
     } else {
         return ke;
     }
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (in_block(s, r, mid, b)) lo = mid; else hi = mid;
+    while (hi_k - lo_k > 1) {
+        const int mid = (lo_k + hi_k) >> 1;
+        if (in_box(s, r, mid, lo, hi)) lo_k = mid; else hi_k = mid;
     }
-    return hi;
+    return hi_k;
 }
 
 __device__ __forceinline__ float code(uint32_t w, int byte) {
@@ -204,6 +219,9 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
     st.limit = false;
     if (!r.hit) return;
     const int N = s.N, B = s.B, P = s.P;
+    float inv_d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) inv_d[i] = __fdividef(1.0f, r.d[i]);
     int k = 0;
     for (;;) {
         if (k >= s.kmax) { st.limit = true; return; }
@@ -212,107 +230,124 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
         int b[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) b[i] = nearest_voxel(lattice_u(r, t, i), N) >> s.lgB;
-        const int slot = __ldg(s.ind + ((b[2] * s.G + b[1]) * s.G + b[0]));
+        const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
+        const int slot = __ldg(s.ind + bi);
         st.blocks++;
-        const int kx = block_exit(s, r, k, b);
-        if (slot >= 0) {
-            const uint8_t* pd = s.pdens + (size_t)slot * s.P3;
-            const uint2* pa = s.patlas + (size_t)slot * s.P3;
-            const int ox = (b[0] << s.lgB) - 1, oy = (b[1] << s.lgB) - 1, oz = (b[2] << s.lgB) - 1;
-            for (int kk = k; kk < kx; ++kk) {
-                st.steps++;
-                const float tk = lattice_t(r, kk);
-                float u[3];
-                int j[3];
+        if (slot < 0) {
+            // every block within Chebyshev distance D-1 of b is empty: leave that box
+            const int D1 = (int)__ldg(s.bdist + bi) - 1;
+            const int lo[3] = {b[0] - D1, b[1] - D1, b[2] - D1};
+            const int hi[3] = {b[0] + D1, b[1] + D1, b[2] + D1};
+            k = box_exit(s, r, inv_d, k, lo, hi);
+            continue;
+        }
+        const int kx = box_exit(s, r, inv_d, k, b, b);
+        const uint8_t* vs = s.vskip + (size_t)slot * s.P3;
+        const uint2* pa = s.patlas + (size_t)slot * s.P3;
+        const int ox = (b[0] << s.lgB) - 1, oy = (b[1] << s.lgB) - 1, oz = (b[2] << s.lgB) - 1;
+        int kk = k;
+        while (kk < kx) {
+            const float tk = lattice_t(r, kk);
+            float u[3];
+            int j[3];
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    u[i] = lattice_u(r, tk, i);
-                    j[i] = nearest_voxel(u[i], N);
-                }
-                // j lies in block b for every kk < kx (block_exit), i.e. l in [1, B]; the
-                // clamp only guards the address
-                const int lx = min(max(j[0] - ox, 1), B), ly = min(max(j[1] - oy, 1), B),
-                          lz = min(max(j[2] - oz, 1), B);
-                const uint8_t qn = __ldg(pd + (lz * P + ly) * P + lx);
-                if (qn == 0) continue;
-                if (TRACE && st.active < trace_cap)
-                    trace[st.active] = ((uint64_t)j[2] * N + (uint64_t)j[1]) * N + (uint64_t)j[0];
-                st.active++;
-                // trilinear stencil on the virtual grid, cell-centred
-                float f[3], g[3];
-                int l0[3];
-                float fl[3];
+            for (int i = 0; i < 3; ++i) {
+                u[i] = lattice_u(r, tk, i);
+                j[i] = nearest_voxel(u[i], N);
+            }
+            // j lies in block b for every kk < kx (box_exit), i.e. l in [1, B]; the
+            // clamp only guards the address
+            const int lx = min(max(j[0] - ox, 1), B), ly = min(max(j[1] - oy, 1), B),
+                      lz = min(max(j[2] - oz, 1), B);
+            const int vd = __ldg(vs + (lz * P + ly) * P + lx);
+            if (vd != 0) {
+                // no voxel of this block within Chebyshev distance vd-1 has density; the
+                // next vd-2 samples move at most vd-1 voxels per axis, so skip them
+                kk += max(1, vd - 1);
+                continue;
+            }
+            if (TRACE && st.active < trace_cap)
+                trace[st.active] = ((uint64_t)j[2] * N + (uint64_t)j[1]) * N + (uint64_t)j[0];
+            st.active++;
+            // trilinear stencil on the virtual grid, cell-centred
+            float f[3], g[3];
+            int l0[3];
+            float fl[3];
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const float x = __fsub_rn(u[i], 0.5f);
-                    fl[i] = floorf(x);
-                    f[i] = __fsub_rn(x, fl[i]);
-                    g[i] = __fsub_rn(1.0f, f[i]);
-                }
-                l0[0] = min(max((int)fl[0] - ox, 0), B);
-                l0[1] = min(max((int)fl[1] - oy, 0), B);
-                l0[2] = min(max((int)fl[2] - oz, 0), B);
-                const uint2* p0 = pa + (l0[2] * P + l0[1]) * P + l0[0];
-                const int PP = P * P;
-                uint2 cv[8];   // index = z*4 + y*2 + x
-                cv[0] = __ldg(p0);
-                cv[1] = __ldg(p0 + 1);
-                cv[2] = __ldg(p0 + P);
-                cv[3] = __ldg(p0 + P + 1);
-                cv[4] = __ldg(p0 + PP);
-                cv[5] = __ldg(p0 + PP + 1);
-                cv[6] = __ldg(p0 + PP + P);
-                cv[7] = __ldg(p0 + PP + P + 1);
-                // binary32 control: density trilinear, x then y then z
-                const float e00 = __fadd_rn(__fmul_rn(code(cv[0].x, 0), g[0]), __fmul_rn(code(cv[1].x, 0), f[0]));
-                const float e10 = __fadd_rn(__fmul_rn(code(cv[2].x, 0), g[0]), __fmul_rn(code(cv[3].x, 0), f[0]));
-                const float e01 = __fadd_rn(__fmul_rn(code(cv[4].x, 0), g[0]), __fmul_rn(code(cv[5].x, 0), f[0]));
-                const float e11 = __fadd_rn(__fmul_rn(code(cv[6].x, 0), g[0]), __fmul_rn(code(cv[7].x, 0), f[0]));
-                const float e0 = __fadd_rn(__fmul_rn(e00, g[1]), __fmul_rn(e10, f[1]));
-                const float e1 = __fadd_rn(__fmul_rn(e01, g[1]), __fmul_rn(e11, f[1]));
-                const float sq = __fadd_rn(__fmul_rn(e0, g[2]), __fmul_rn(e1, f[2]));
-                const float od = __fmul_rn(sq, s.kappa);
-                st.tau = __fadd_rn(st.tau, od);
-                // compositing (Eqs. 2, 5, 6)
-                const float e = expf(-od);
-                const float wk = st.T * (1.0f - e);
-                st.T *= e;
-                float tw[8];
+            for (int i = 0; i < 3; ++i) {
+                const float x = __fsub_rn(u[i], 0.5f);
+                fl[i] = floorf(x);
+                f[i] = __fsub_rn(x, fl[i]);
+                g[i] = __fsub_rn(1.0f, f[i]);
+            }
+            l0[0] = min(max((int)fl[0] - ox, 0), B);
+            l0[1] = min(max((int)fl[1] - oy, 0), B);
+            l0[2] = min(max((int)fl[2] - oz, 0), B);
+            const uint2* p0 = pa + (l0[2] * P + l0[1]) * P + l0[0];
+            const int PP = P * P;
+            uint2 cv[8];   // index = z*4 + y*2 + x
+            cv[0] = __ldg(p0);
+            cv[1] = __ldg(p0 + 1);
+            cv[2] = __ldg(p0 + P);
+            cv[3] = __ldg(p0 + P + 1);
+            cv[4] = __ldg(p0 + PP);
+            cv[5] = __ldg(p0 + PP + 1);
+            cv[6] = __ldg(p0 + PP + P);
+            cv[7] = __ldg(p0 + PP + P + 1);
+            // binary32 control: density trilinear, x then y then z
+            const float e00 = __fadd_rn(__fmul_rn(code(cv[0].x, 0), g[0]), __fmul_rn(code(cv[1].x, 0), f[0]));
+            const float e10 = __fadd_rn(__fmul_rn(code(cv[2].x, 0), g[0]), __fmul_rn(code(cv[3].x, 0), f[0]));
+            const float e01 = __fadd_rn(__fmul_rn(code(cv[4].x, 0), g[0]), __fmul_rn(code(cv[5].x, 0), f[0]));
+            const float e11 = __fadd_rn(__fmul_rn(code(cv[6].x, 0), g[0]), __fmul_rn(code(cv[7].x, 0), f[0]));
+            const float e0 = __fadd_rn(__fmul_rn(e00, g[1]), __fmul_rn(e10, f[1]));
+            const float e1 = __fadd_rn(__fmul_rn(e01, g[1]), __fmul_rn(e11, f[1]));
+            const float sq = __fadd_rn(__fmul_rn(e0, g[2]), __fmul_rn(e1, f[2]));
+            const float od = __fmul_rn(sq, s.kappa);
+            st.tau = __fadd_rn(st.tau, od);
+            // compositing (Eqs. 2, 5, 6)
+            const float e = expf(-od);
+            const float wk = st.T * (1.0f - e);
+            st.T *= e;
+            float tw[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    tw[c] = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
+            for (int c = 0; c < 8; ++c)
+                tw[c] = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float w = wk * tw[c];
+                st.acc[0] += w * code(cv[c].x, 1);
+                st.acc[1] += w * code(cv[c].x, 2);
+                st.acc[2] += w * code(cv[c].x, 3);
+                st.acc[3] += w * code(cv[c].y, 0);
+                st.acc[4] += w * code(cv[c].y, 1);
+                st.acc[5] += w * code(cv[c].y, 2);
+                st.acc[6] += w * code(cv[c].y, 3);
+            }
+            if (GRAD) {
+                const int B3 = B * B * B;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
+                    const int X = min(max((int)fl[0] + (c & 1), 0), N - 1);
+                    const int Y = min(max((int)fl[1] + ((c >> 1) & 1), 0), N - 1);
+                    const int Z = min(max((int)fl[2] + ((c >> 2) & 1), 0), N - 1);
+                    const int cs = __ldg(s.ind + (((Z >> s.lgB) * s.G + (Y >> s.lgB)) * s.G + (X >> s.lgB)));
+                    if (cs < 0) continue;
+                    const int loc = (((Z & (B - 1)) * B) + (Y & (B - 1))) * B + (X & (B - 1));
+                    float* gp = grad_atlas + ((size_t)cs * B3 + loc) * 8;
                     const float w = wk * tw[c];
-                    st.acc[0] += w * code(cv[c].x, 1);
-                    st.acc[1] += w * code(cv[c].x, 2);
-                    st.acc[2] += w * code(cv[c].x, 3);
-                    st.acc[3] += w * code(cv[c].y, 0);
-                    st.acc[4] += w * code(cv[c].y, 1);
-                    st.acc[5] += w * code(cv[c].y, 2);
-                    st.acc[6] += w * code(cv[c].y, 3);
+                    atomicAdd(reinterpret_cast<float4*>(gp),
+                              make_float4(0.0f, w * gfeat[0], w * gfeat[1], w * gfeat[2]));
+                    atomicAdd(reinterpret_cast<float4*>(gp + 4),
+                              make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
                 }
-                if (GRAD) {
-                    const int B3 = B * B * B;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const int X = min(max((int)fl[0] + (c & 1), 0), N - 1);
-                        const int Y = min(max((int)fl[1] + ((c >> 1) & 1), 0), N - 1);
-                        const int Z = min(max((int)fl[2] + ((c >> 2) & 1), 0), N - 1);
-                        const int cs = __ldg(s.ind + (((Z >> s.lgB) * s.G + (Y >> s.lgB)) * s.G + (X >> s.lgB)));
-                        if (cs < 0) continue;
-                        const int loc = (((Z & (B - 1)) * B) + (Y & (B - 1))) * B + (X & (B - 1));
-                        float* gp = grad_atlas + ((size_t)cs * B3 + loc) * 8;
-                        const float w = wk * tw[c];
-                        atomicAdd(reinterpret_cast<float4*>(gp),
-                                  make_float4(0.0f, w * gfeat[0], w * gfeat[1], w * gfeat[2]));
-                        atomicAdd(reinterpret_cast<float4*>(gp + 4),
-                                  make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
-                    }
-                }
-                if (st.tau > s.taumax) return;
             }
+            if (st.tau > s.taumax) {
+                st.steps += kk - k + 1;
+                return;
+            }
+            ++kk;
         }
+        st.steps += kx - k;
         k = kx;
     }
 }
@@ -421,7 +456,13 @@ cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_
 cudaError_t launch_validate(const int32_t* ind, int64_t n_ind, int64_t nb, int32_t* blk_of_slot, int32_t* err,
                             cudaStream_t st);
 cudaError_t launch_build_padded(const int32_t* ind, const int32_t* blk_of_slot, const uint8_t* atlas, int64_t nb,
-                                int N, int B, int lgB, uint8_t* pdens, uint2* patlas, cudaStream_t st);
+                                int N, int B, int lgB, uint2* patlas, cudaStream_t st);
+// Chebyshev distance maps (three separable passes, distances capped at `cap`):
+// block level over the G^3 indirection grid, voxel level inside each stored block.
+cudaError_t launch_block_distance(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
+                                  uint8_t* bdist, cudaStream_t st);
+cudaError_t launch_voxel_distance(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
+                                  uint8_t* vskip, cudaStream_t st);
 
 struct PersistentParams {
     snerg_camera cams[kMaxCams];

@@ -1,10 +1,12 @@
-// snerg_prep.cu -- scene set-up kernels: validate the indirection grid (Sec. 5.1) and
-// build the device layout of the atlas (apron-padded blocks + a split density plane).
+// snerg_prep.cu -- scene set-up kernels: validate the indirection grid (Sec. 5.1),
+// build the device layout of the atlas (apron-padded blocks) and the two Chebyshev
+// distance maps the march uses to skip empty space.
 //
 // The paper's viewer keeps density in its own 8-bit texture so that empty space inside
-// occupied blocks costs one byte per sample (App. A); the density plane here plays that
-// role. The 1-voxel apron makes every trilinear stencil of a sample a fetch from one
-// block: atlas neighbours are not spatial neighbours (Sec. 5.1), so without it a sample
+// occupied blocks costs one byte per sample (App. A); the voxel distance plane here
+// plays that role and, being a distance rather than a code, also says how many of the
+// following samples are certainly empty. The 1-voxel apron makes every trilinear
+// stencil of a sample a fetch from one block: atlas neighbours are not spatial neighbours (Sec. 5.1), so without it a sample
 // near a block face would need up to 8 indirection lookups.
 #include "snerg_internal.cuh"
 
@@ -28,7 +30,7 @@ __global__ void validate_kernel(const int32_t* __restrict__ ind, int64_t n_ind, 
 // block supplies the value, or 0 if that block is empty.
 __global__ void build_padded_kernel(const int32_t* __restrict__ ind, const int32_t* __restrict__ blk_of_slot,
                                     const uint2* __restrict__ atlas, int64_t nb, int N, int B, int lgB,
-                                    uint8_t* __restrict__ pdens, uint2* __restrict__ patlas) {
+                                    uint2* __restrict__ patlas) {
     const int P = B + 2, P3 = P * P * P, G = N >> lgB;
     const int64_t total = nb * (int64_t)P3;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -49,8 +51,102 @@ __global__ void build_padded_kernel(const int32_t* __restrict__ ind, const int32
             }
         }
         patlas[t] = v;
-        pdens[t] = (uint8_t)(v.x & 0xffu);
     }
+}
+
+// ---------------------------------------------------------------------------------
+// Chebyshev (L-infinity) distance transform of cubes of side n, in three separable
+// passes: along one axis, out(p) = min over q on p's line of max(|q - p|, in(q)),
+// capped at `cap`. Starting from in = 0 on occupied cells and cap elsewhere, after the
+// x, y and z passes out(p) = min over occupied q of max_i |q_i - p_i| (max distributes
+// over min, so the passes compose). The scan walks outwards from p and stops once the
+// offset reaches the best value found, so its cost is the distance itself.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ int dt_line(const uint8_t* __restrict__ in, int64_t base, int64_t stride, int pos, int n,
+                                       int cap) {
+    int best = min((int)in[base + pos * stride], cap);
+    for (int d = 1; d < best; ++d) {
+        const int a = pos - d, b = pos + d;
+        if (a < 0 && b >= n) break;
+        if (a >= 0) best = min(best, max(d, (int)in[base + a * stride]));
+        if (b < n) best = min(best, max(d, (int)in[base + b * stride]));
+    }
+    return best;
+}
+
+// axis: 0 = x (stride 1), 1 = y (stride n), 2 = z (stride n^2); cubes are contiguous
+__global__ void dt_pass_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int n, int64_t ncubes,
+                               int axis, int cap) {
+    const int64_t n3 = (int64_t)n * n * n;
+    const int64_t total = ncubes * n3;
+    const int64_t stride = axis == 0 ? 1 : (axis == 1 ? n : (int64_t)n * n);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cube = t / n3;
+        const int r = (int)(t - cube * n3);
+        const int c[3] = {r % n, (r / n) % n, r / (n * n)};
+        const int pos = c[axis];
+        const int64_t base = t - (int64_t)pos * stride;
+        out[t] = (uint8_t)dt_line(in, base, stride, pos, n, cap);
+    }
+}
+
+// 0 where the block is occupied, cap elsewhere
+__global__ void block_seed_kernel(const int32_t* __restrict__ ind, int64_t n, int cap, uint8_t* __restrict__ out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = ind[t] >= 0 ? 0 : (uint8_t)cap;
+}
+
+// 0 where the voxel's density code is non-zero, cap elsewhere (unpadded [nb][B^3])
+__global__ void voxel_seed_kernel(const uint8_t* __restrict__ atlas, int64_t n, int cap, uint8_t* __restrict__ out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = atlas[t * 8] != 0 ? 0 : (uint8_t)cap;
+}
+
+// z pass of the voxel transform, written into the padded plane (apron cells = 255)
+__global__ void dt_pass_z_padded_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ vskip, int B,
+                                        int64_t nb, int cap) {
+    const int P = B + 2, P3 = P * P * P;
+    const int64_t B3 = (int64_t)B * B * B;
+    const int64_t total = nb * P3;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = t / P3;
+        const int r = (int)(t - slot * P3);
+        const int px = r % P - 1, py = (r / P) % P - 1, pz = r / (P * P) - 1;
+        uint8_t v = 255;
+        if (px >= 0 && py >= 0 && pz >= 0 && px < B && py < B && pz < B) {
+            const int64_t base = slot * B3 + (int64_t)py * B + px;
+            v = (uint8_t)dt_line(in, base, (int64_t)B * B, pz, B, cap);
+        }
+        vskip[t] = v;
+    }
+}
+
+static unsigned grid_for(int64_t n) {
+    const int64_t b = (n + 255) / 256;
+    return (unsigned)(b < 1048576 ? (b > 0 ? b : 1) : 1048576);
+}
+
+cudaError_t launch_block_distance(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
+                                  uint8_t* bdist, cudaStream_t st) {
+    const int64_t n = (int64_t)G * G * G;
+    block_seed_kernel<<<grid_for(n), 256, 0, st>>>(ind, n, cap, tmp0);
+    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, tmp1, G, 1, 0, cap);
+    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp1, tmp0, G, 1, 1, cap);
+    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, bdist, G, 1, 2, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_voxel_distance(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
+                                  uint8_t* vskip, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    const int64_t n = nb * (int64_t)B * B * B;
+    const int cap = 255;
+    voxel_seed_kernel<<<grid_for(n), 256, 0, st>>>(atlas, n, cap, tmp0);
+    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, tmp1, B, nb, 0, cap);
+    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp1, tmp0, B, nb, 1, cap);
+    dt_pass_z_padded_kernel<<<grid_for(nb * (int64_t)(B + 2) * (B + 2) * (B + 2)), 256, 0, st>>>(tmp0, vskip, B, nb,
+                                                                                              cap);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_validate(const int32_t* ind, int64_t n_ind, int64_t nb, int32_t* blk_of_slot, int32_t* err,
@@ -62,12 +158,11 @@ cudaError_t launch_validate(const int32_t* ind, int64_t n_ind, int64_t nb, int32
 }
 
 cudaError_t launch_build_padded(const int32_t* ind, const int32_t* blk_of_slot, const uint8_t* atlas, int64_t nb,
-                                int N, int B, int lgB, uint8_t* pdens, uint2* patlas, cudaStream_t st) {
+                                int N, int B, int lgB, uint2* patlas, cudaStream_t st) {
     if (nb <= 0) return cudaSuccess;
     const int64_t total = nb * (int64_t)(B + 2) * (B + 2) * (B + 2);
-    const int64_t blocks = (total + 255) / 256;
-    build_padded_kernel<<<(unsigned)(blocks < 1048576 ? blocks : 1048576), 256, 0, st>>>(
-        ind, blk_of_slot, reinterpret_cast<const uint2*>(atlas), nb, N, B, lgB, pdens, patlas);
+    build_padded_kernel<<<grid_for(total), 256, 0, st>>>(ind, blk_of_slot, reinterpret_cast<const uint2*>(atlas), nb,
+                                                          N, B, lgB, patlas);
     return cudaGetLastError();
 }
 
