@@ -8,12 +8,14 @@ namespace snerg {
 // Warp w of a 128-thread CTA covers an 8x4 pixel packet of the CTA's 16x8 tile, so the
 // 32 rays of a warp are neighbours on screen and walk neighbouring voxels together.
 template <bool DBG>
-__global__ void __launch_bounds__(128) render_image_kernel(const DevScene s, const snerg_camera cam,
+__global__ void __launch_bounds__(128, 8) render_image_kernel(const DevScene s, const snerg_camera cam,
                                                            const float* __restrict__ mlp,
                                                            float* __restrict__ rgb, const DebugOut dbg) {
-    __shared__ float sW[kNParam];
-    load_mlp_smem(sW, mlp);
+    __shared__ __align__(16) float sW[kNParam + 1];
+    __shared__ float sX[128 * kXStride];
+    load_mlp_smem_t(sW, mlp);
     __syncthreads();
+    float* xrow = sX + threadIdx.x * kXStride;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
@@ -27,7 +29,7 @@ __global__ void __launch_bounds__(128) render_image_kernel(const DevScene s, con
         march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
     record_status(s, st);
     float c[3], aux[kAuxCh];
-    finish_ray(s, sW, r, st, c, aux);
+    finish_ray(s, sW, xrow, r, st, c, aux);
     rgb[pix * 3 + 0] = c[0];
     rgb[pix * 3 + 1] = c[1];
     rgb[pix * 3 + 2] = c[2];
@@ -44,13 +46,15 @@ __global__ void __launch_bounds__(128) render_image_kernel(const DevScene s, con
 }
 
 template <bool DBG>
-__global__ void __launch_bounds__(128) render_rays_kernel(const DevScene s, const __grid_constant__ CamTable cams,
+__global__ void __launch_bounds__(128, 8) render_rays_kernel(const DevScene s, const __grid_constant__ CamTable cams,
                                                           int32_t n_cams, const int32_t* __restrict__ pix,
                                                           int64_t n, const float* __restrict__ mlp,
                                                           float* __restrict__ rgb, const DebugOut dbg) {
-    __shared__ float sW[kNParam];
-    load_mlp_smem(sW, mlp);
+    __shared__ __align__(16) float sW[kNParam + 1];
+    __shared__ float sX[128 * kXStride];
+    load_mlp_smem_t(sW, mlp);
     __syncthreads();
+    float* xrow = sX + threadIdx.x * kXStride;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int ci = __ldg(pix + 3 * i), px = __ldg(pix + 3 * i + 1), py = __ldg(pix + 3 * i + 2);
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(128) render_rays_kernel(const DevScene s, cons
         march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
     record_status(s, st);
     float c[3], aux[kAuxCh];
-    finish_ray(s, sW, r, st, c, aux);
+    finish_ray(s, sW, xrow, r, st, c, aux);
     rgb[i * 3 + 0] = c[0];
     rgb[i * 3 + 1] = c[1];
     rgb[i * 3 + 2] = c[2];
@@ -89,14 +93,16 @@ __global__ void __launch_bounds__(128) render_rays_kernel(const DevScene s, cons
 // (tile_w x tile_h pixels of one camera) from a global counter until the queue is empty,
 // and renders each item in warp_w x warp_h packets of 32 rays. The counter is zeroed by
 // the launch sequence (a memset node of the captured graph) before every launch.
-__global__ void __launch_bounds__(256) render_persistent_kernel(const DevScene s,
+__global__ void __launch_bounds__(128, 8) render_persistent_kernel(const DevScene s,
                                                                 const __grid_constant__ PersistentParams p,
                                                                 const float* __restrict__ mlp,
                                                                 float* __restrict__ rgb,
                                                                 int32_t* __restrict__ queue) {
-    __shared__ float sW[kNParam];
-    load_mlp_smem(sW, mlp);
+    __shared__ __align__(16) float sW[kNParam + 1];
+    __shared__ float sX[128 * kXStride];
+    load_mlp_smem_t(sW, mlp);
     __syncthreads();
+    float* xrow = sX + threadIdx.x * kXStride;
     const int lane = threadIdx.x & 31;
     const int passes_x = p.tile_w / p.warp_w;
     const int passes = passes_x * (p.tile_h / p.warp_h);
@@ -123,7 +129,7 @@ __global__ void __launch_bounds__(256) render_persistent_kernel(const DevScene s
                 march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
                 record_status(s, st);
                 float c[3], aux[kAuxCh];
-                finish_ray(s, sW, r, st, c, aux);
+                finish_ray(s, sW, xrow, r, st, c, aux);
                 const int64_t o = (cam.out_offset + (int64_t)py * cam.W + px) * 3;
                 rgb[o + 0] = c[0];
                 rgb[o + 1] = c[1];

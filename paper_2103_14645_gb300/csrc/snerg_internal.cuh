@@ -405,9 +405,105 @@ __device__ __forceinline__ void load_mlp_smem(float* sW, const float* mlp) {
         sW[i] = __ldg(mlp + i);
 }
 
-// Finish one ray: colour = C_d + residual + T bg (residual only if something was composited).
-__device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, const Ray& r, const MarchState& st,
-                                           float rgb[3], float aux[kAuxCh]) {
+// ---------------------------------------------------------------------------------
+// Forward-kernel form of the same MLP, built to stay small in registers and code:
+// weights sit in shared memory with W1 and W2 transposed (rows of 16 outputs, read with
+// uniform 128-bit loads), the 34-float input row of each thread is staged in shared
+// memory and streamed through a rolled loop, and the direction encoding takes one
+// sincosf per axis and the double-angle identities for the higher octaves.
+// Layout (floats): W1^T[34][16] | b1[16] | W2^T[16][16] | b2[16] | W3[3][16] | b3[3]
+// (the offsets kOff* are those of the flat layout; only W1 and W2 are transposed).
+// ---------------------------------------------------------------------------------
+constexpr int kXStride = 35;   // per-thread input row stride in shared memory (odd: no bank conflicts)
+
+__device__ __forceinline__ void load_mlp_smem_t(float* sW, const float* mlp) {
+    const int nt = blockDim.x * blockDim.y;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    for (int i = tid; i < kNParam; i += nt) {
+        int dst = i;
+        if (i < kOffB1) {                     // W1[o][k] -> W1^T[k][o]
+            const int o = i / kMlpIn, k = i % kMlpIn;
+            dst = kOffW1 + k * kMlpH + o;
+        } else if (i >= kOffW2 && i < kOffB2) {   // W2[o][k] -> W2^T[k][o]
+            const int o = (i - kOffW2) / kMlpH, k = (i - kOffW2) % kMlpH;
+            dst = kOffW2 + k * kMlpH + o;
+        }
+        sW[dst] = __ldg(mlp + i);
+    }
+}
+
+__device__ __forceinline__ void fma16(float h[16], const float* w, float x) {
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 v = w4[q];
+        h[4 * q + 0] = fmaf(v.x, x, h[4 * q + 0]);
+        h[4 * q + 1] = fmaf(v.y, x, h[4 * q + 1]);
+        h[4 * q + 2] = fmaf(v.z, x, h[4 * q + 2]);
+        h[4 * q + 3] = fmaf(v.w, x, h[4 * q + 3]);
+    }
+}
+
+__device__ __forceinline__ void load16(float h[16], const float* w) {
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 v = w4[q];
+        h[4 * q + 0] = v.x;
+        h[4 * q + 1] = v.y;
+        h[4 * q + 2] = v.z;
+        h[4 * q + 3] = v.w;
+    }
+}
+
+// x = [C_d, V, d, sin(2^l d), cos(2^l d) for l = 0..3] written to the thread's row
+__device__ __forceinline__ void stage_mlp_input(float* xrow, const float cd[3], const float v[4], const float d[3]) {
+    xrow[0] = cd[0]; xrow[1] = cd[1]; xrow[2] = cd[2];
+    xrow[3] = v[0]; xrow[4] = v[1]; xrow[5] = v[2]; xrow[6] = v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        xrow[7 + i] = d[i];
+        float sv, cv;
+        sincosf(d[i], &sv, &cv);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            xrow[10 + 6 * l + i] = sv;
+            xrow[13 + 6 * l + i] = cv;
+            const float s2 = 2.0f * sv * cv;          // sin 2a
+            const float c2 = (cv - sv) * (cv + sv);   // cos 2a
+            sv = s2;
+            cv = c2;
+        }
+    }
+}
+
+__device__ __forceinline__ void mlp_residual(const float* sW, const float* xrow, float res[3]) {
+    float h[16];
+    load16(h, sW + kOffB1);
+#pragma unroll 2
+    for (int i = 0; i < kMlpIn; ++i) fma16(h, sW + kOffW1 + i * kMlpH, xrow[i]);
+#pragma unroll
+    for (int o = 0; o < 16; ++o) h[o] = fmaxf(h[o], 0.0f);
+    float h2[16];
+    load16(h2, sW + kOffB2);
+#pragma unroll
+    for (int i = 0; i < kMlpH; ++i) fma16(h2, sW + kOffW2 + i * kMlpH, h[i]);
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) {
+        float w3[16];
+        load16(w3, sW + kOffW3 + o * kMlpH);
+        float acc = sW[kOffB3 + o];
+#pragma unroll
+        for (int i = 0; i < kMlpH; ++i) acc = fmaf(w3[i], fmaxf(h2[i], 0.0f), acc);
+        res[o] = 1.0f / (1.0f + expf(-acc));
+    }
+}
+
+// Finish one ray: colour = C_d + residual + T bg (residual only if something was
+// composited). xrow: this thread's kXStride-float row of shared memory; sW: weights in
+// the transposed layout of load_mlp_smem_t.
+__device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, float* xrow, const Ray& r,
+                                           const MarchState& st, float rgb[3], float aux[kAuxCh]) {
     const float inv255 = 1.0f / 255.0f;
     float cd[3], v[4];
 #pragma unroll
@@ -416,12 +512,11 @@ __device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, c
     for (int c = 0; c < 4; ++c) v[c] = st.acc[3 + c] * inv255;
     float res[3] = {0.0f, 0.0f, 0.0f};
     if (st.active > 0) {
-        float x[kMlpIn];
-        mlp_input(cd, v, r.d, x);
-        MlpAct a;
-        mlp_forward(sW, x, a);
+        stage_mlp_input(xrow, cd, v, r.d);
+        float m[3];
+        mlp_residual(sW, xrow, m);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) res[c] = cd[c] + a.res[c];
+        for (int c = 0; c < 3; ++c) res[c] = cd[c] + m[c];
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) rgb[c] = res[c] + st.T * s.bg[c];
