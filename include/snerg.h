@@ -142,6 +142,35 @@ snerg_status snerg_render_backward(snerg_handle h, const snerg_camera* cams, int
                                    const float* d_grad_rgb, float* d_grad_atlas,
                                    float* d_grad_mlp, void* stream);
 
+/* Ray-list render for callers that cannot allocate device memory. The paper has no
+ * counterpart: this entry point exists for callers such as a plug-in inside a host
+ * application that owns all GPU memory through its own pool and forbids cudaMalloc, a
+ * real-time loop that cannot afford the implicit device synchronisation of
+ * cudaMalloc/cudaFree, or a sandboxed caller that is only handed its input and output
+ * buffers. It needs no handle and no workspace, and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   desc, d_indirection, d_atlas, num_blocks : the scene, laid out as for snerg_create;
+ *       read in place during the call (not copied, not validated: entries must lie in
+ *       [-1, num_blocks); an entry >= num_blocks is reported and read as empty).
+ *   cams, n_cams, d_pix, n, d_mlp, d_rgb : as for snerg_render_rays (same colours up to
+ *       floating-point rounding; it renders from the unpadded atlas without the voxel
+ *       distance map).
+ *   d_status : nullable device int32; receives SNERG_OK or the first device-side error
+ *       of this call (SNERG_E_INVAL for a bad pixel or atlas entry).
+ * Limit: N / B <= 64; larger grids return SNERG_E_UNSUPPORTED.
+ * Scratch: a status word and the block-level empty-space distance map live in one static
+ * device array of 786,688 bytes that every GPU loading this library holds until the
+ * process exits. The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current): make that first call before any
+ * stream capture. All calls share the array and each call rewrites it, so calls whose
+ * work overlaps on the GPU (different streams or host threads) race; serialise them.
+ * Asynchronous on `stream`. */
+snerg_status snerg_render_rays_noalloc(const snerg_scene_desc* desc, const int32_t* d_indirection,
+                                       const uint8_t* d_atlas, int64_t num_blocks,
+                                       const snerg_camera* cams, int32_t n_cams,
+                                       const int32_t* d_pix, int64_t n, const float* d_mlp,
+                                       float* d_rgb, int32_t* d_status, void* stream);
+
 /* SYNCHRONISES `stream`, returns and clears the device status word (SNERG_OK or the
  * first device error recorded since the last call), or SNERG_E_CUDA if the stream
  * reports an asynchronous CUDA error. */

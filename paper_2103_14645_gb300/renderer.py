@@ -25,7 +25,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error"
 
 EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_render_rays",
             "snerg_render_backward", "snerg_last_status", "snerg_launch_count",
-            "snerg_persistent_config", "snerg_destroy", "snerg_status_str"]
+            "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc"]
 
 
 class SnergError(RuntimeError):
@@ -78,6 +78,8 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_destroy.restype = None
     lib.snerg_status_str.argtypes = [ctypes.c_int]
     lib.snerg_status_str.restype = ctypes.c_char_p
+    lib.snerg_render_rays_noalloc.argtypes = [P, P, P, i64, P, i32, P, i64, P, P, P, P]
+    lib.snerg_render_rays_noalloc.restype = ctypes.c_int
     _LIB = lib
     return lib
 
