@@ -128,6 +128,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_cameras(sc, rank: int):
+    """Weak scaling: rank 0 renders the workload's own view, every other rank its own
+    seeded 800x800 view of the same grid (rays are independent; no data is exchanged)."""
+    from paper_2103_14645_gb300 import synth
+    if rank == 0:
+        return sc.cameras
+    return synth.orbit_cameras(np.random.default_rng(9000 + rank), [(800, 800)], synth.CAM_RADIUS)
+
+
+def reduce_max(value: float, device) -> float:
+    """Max over ranks of a per-rank time (identity without a process group)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mrays(world_size: int, rays_per_rank: int, t_max_ms: float) -> float:
+    """Aggregate throughput: all ranks' rays over the slowest rank's step time."""
+    return world_size * rays_per_rank / (t_max_ms * 1e-3) / 1e6
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -207,9 +232,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
 
     sc = synth.make_scene("shell1024")
-    cams = sc.cameras
-    if rank > 0:     # each rank renders its own seeded view of the same grid
-        cams = synth.orbit_cameras(np.random.default_rng(9000 + rank), [(800, 800)], synth.CAM_RADIUS)
+    cams = rank_cameras(sc, rank)
     r = renderer.Renderer.from_scene(sc, dev)
     mlp = torch.from_numpy(sc.mlp).to(dev)
     out = torch.empty((800 * 800, 3), dtype=torch.float32, device=dev)
@@ -230,12 +253,8 @@ def run_ours(args, ws, rank, local):
     barrier()
     launches = r.launches - l0 - args.warmup
     t_step = float(np.mean(ms))
-    t_max = t_step
-    if dist:
-        t = torch.tensor([t_step], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ws * n_rays / (t_max * 1e-3) / 1e6
+    t_max = reduce_max(t_step, dev)
+    value = whole_job_mrays(ws, n_rays, t_max)
 
     # end to end through the public API with host buffers: camera record in, image out
     host_out = torch.empty((n_rays, 3), dtype=torch.float32, pin_memory=True)
@@ -247,7 +266,7 @@ def run_ours(args, ws, rank, local):
     barrier()
     ms_e2e = time_steps(e2e_step, args.steps, args.warmup, stream, flush)
     barrier()
-    e2e = ws * n_rays / (float(np.mean(ms_e2e)) * 1e-3) / 1e6
+    e2e = whole_job_mrays(ws, n_rays, reduce_max(float(np.mean(ms_e2e)), dev))
 
     extra = {}
     if not args.no_extra:
