@@ -8,35 +8,106 @@
 // into the FP32 gradient atlas with vector atomics. Because density is frozen the
 // composite weights w_k depend only on the samples before k, so the second pass walks
 // the ray in forward order and needs no per-sample state. MLP weight gradients are
-// summed across the warp with shuffles, across the CTA in shared memory, and reach
-// global memory with one atomic per parameter per CTA.
+// summed over the CTA's rays from activations staged in shared memory and reach global
+// memory with one atomic per parameter per CTA.
 #include "snerg_internal.cuh"
 
 namespace snerg {
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Per-thread shared-memory row (floats): x[34] | h1[16] | h2[16] | g1[16] | g2[16] | gz[3]
+// (MLP input, hidden activations, their adjoints and the output adjoint). 101 is odd,
+// so rows of neighbouring threads fall in different banks.
+constexpr int kBwdThreads = 128;
+constexpr int kRowX = 0, kRowH1 = 34, kRowH2 = 50, kRowG1 = 66, kRowG2 = 82, kRowGZ = 98, kRow = 101;
+constexpr int kWFloats = 884;     // transposed weights (883) rounded up to a 16-byte multiple
+
+size_t backward_smem_bytes() { return (size_t)(kWFloats + kBwdThreads * kRow) * sizeof(float); }
+
+// MLP forward keeping activations, then its adjoint for dL/dres = g; writes h1, h2, g1,
+// g2, gz into the row and returns dL/dx for the 7 composited inputs (C_d, V).
+__device__ __forceinline__ void mlp_forward_backward(const float* sW, float* row, const float g[3], float gx[7]) {
+    float h[16];
+    load16(h, sW + kOffB1);
+#pragma unroll 2
+    for (int i = 0; i < kMlpIn; ++i) fma16(h, sW + kOffW1 + i * kMlpH, row[kRowX + i]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int o = 0; o < 16; ++o) {
+        h[o] = fmaxf(h[o], 0.0f);
+        row[kRowH1 + o] = h[o];
+    }
+    float h2[16];
+    load16(h2, sW + kOffB2);
+#pragma unroll
+    for (int i = 0; i < kMlpH; ++i) fma16(h2, sW + kOffW2 + i * kMlpH, h[i]);
+#pragma unroll
+    for (int o = 0; o < 16; ++o) {
+        h2[o] = fmaxf(h2[o], 0.0f);
+        row[kRowH2 + o] = h2[o];
+    }
+    float gz[3];
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) {
+        float acc = sW[kOffB3 + o];
+#pragma unroll
+        for (int i = 0; i < kMlpH; ++i) acc = fmaf(sW[kOffW3 + o * kMlpH + i], h2[i], acc);
+        const float r = 1.0f / (1.0f + expf(-acc));
+        gz[o] = g[o] * r * (1.0f - r);                 // sigmoid'
+        row[kRowGZ + o] = gz[o];
+    }
+    float g2[16];
+#pragma unroll
+    for (int k = 0; k < kMlpH; ++k) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int o = 0; o < kMlpOut; ++o) acc = fmaf(sW[kOffW3 + o * kMlpH + k], gz[o], acc);
+        g2[k] = h2[k] > 0.0f ? acc : 0.0f;           // ReLU'
+        row[kRowG2 + k] = g2[k];
+    }
+    // g1 = W2^T g2 masked by ReLU', one hidden unit at a time (rolled: keeps the weight
+    // loads from being hoisted into registers), written to the row
+#pragma unroll 1
+    for (int k = 0; k < kMlpH; ++k) {
+        const float4* w = reinterpret_cast<const float4*>(sW + kOffW2 + k * kMlpH);   // W2^T[k][o] = W2[o][k]
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = w[q];
+            acc = fmaf(v.x, g2[4 * q], acc);
+            acc = fmaf(v.y, g2[4 * q + 1], acc);
+            acc = fmaf(v.z, g2[4 * q + 2], acc);
+            acc = fmaf(v.w, g2[4 * q + 3], acc);
+        }
+        row[kRowG1 + k] = row[kRowH1 + k] > 0.0f ? acc : 0.0f;
+    }
+    float g1[16];
+#pragma unroll
+    for (int k = 0; k < kMlpH; ++k) g1[k] = row[kRowG1 + k];
+#pragma unroll 1
+    for (int k = 0; k < 7; ++k) {
+        const float4* w = reinterpret_cast<const float4*>(sW + kOffW1 + k * kMlpH);   // W1^T[k][o] = W1[o][k]
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = w[q];
+            acc = fmaf(v.x, g1[4 * q], acc);
+            acc = fmaf(v.y, g1[4 * q + 1], acc);
+            acc = fmaf(v.z, g1[4 * q + 2], acc);
+            acc = fmaf(v.w, g1[4 * q + 3], acc);
+        }
+        gx[k] = acc;
+    }
 }
 
-__device__ __forceinline__ void acc_param(float* sG, int idx, float v, int lane) {
-    v = warp_sum(v);
-    if (lane == 0 && v != 0.0f) atomicAdd(sG + idx, v);
-}
-
-__global__ void __launch_bounds__(128) backward_rays_kernel(const DevScene s, const __grid_constant__ CamTable cams,
-                                                            int32_t n_cams, const int32_t* __restrict__ pix,
-                                                            int64_t n, const float* __restrict__ mlp,
-                                                            const float* __restrict__ grad_rgb,
-                                                            float* __restrict__ grad_atlas,
-                                                            float* __restrict__ grad_mlp) {
-    __shared__ float sW[kNParam];
-    __shared__ float sG[kNParam];
-    load_mlp_smem(sW, mlp);
-    for (int p = threadIdx.x; p < kNParam; p += blockDim.x) sG[p] = 0.0f;
+__global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
+    const DevScene s, const __grid_constant__ CamTable cams, int32_t n_cams, const int32_t* __restrict__ pix,
+    int64_t n, const float* __restrict__ mlp, const float* __restrict__ grad_rgb, float* __restrict__ grad_atlas,
+    float* __restrict__ grad_mlp) {
+    extern __shared__ __align__(16) float smem[];
+    float* sW = smem;
+    float* rows = smem + kWFloats;
+    load_mlp_smem_t(sW, mlp);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    float* row = rows + threadIdx.x * kRow;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
     Ray r;
@@ -54,78 +125,43 @@ __global__ void __launch_bounds__(128) backward_rays_kernel(const DevScene s, co
         record_status(s, st);
     }
     const bool active = st.active > 0;
-
-    // forward MLP with the activations kept for the adjoint
-    float x[kMlpIn];
-    MlpAct a;
     float g[3] = {0.0f, 0.0f, 0.0f};
+    float gx[7];
     if (active) {
         const float inv255 = 1.0f / 255.0f;
-        float cd[3] = {st.acc[0] * inv255, st.acc[1] * inv255, st.acc[2] * inv255};
-        float v[4] = {st.acc[3] * inv255, st.acc[4] * inv255, st.acc[5] * inv255, st.acc[6] * inv255};
-        mlp_input(cd, v, r.d, x);
-        mlp_forward(sW, x, a);
+        const float cd[3] = {st.acc[0] * inv255, st.acc[1] * inv255, st.acc[2] * inv255};
+        const float v[4] = {st.acc[3] * inv255, st.acc[4] * inv255, st.acc[5] * inv255, st.acc[6] * inv255};
+        stage_mlp_input(row + kRowX, cd, v, r.d);
         g[0] = __ldg(grad_rgb + 3 * i);
         g[1] = __ldg(grad_rgb + 3 * i + 1);
         g[2] = __ldg(grad_rgb + 3 * i + 2);
+        mlp_forward_backward(sW, row, g, gx);
     } else {
-#pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) x[k] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < kMlpH; ++k) a.h1[k] = a.h2[k] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < kMlpOut; ++k) a.res[k] = 0.0f;
-    }
-    // adjoint: sigmoid, layer 3, ReLU, layer 2, ReLU, layer 1
-    float gz[kMlpOut], gh2[kMlpH], gh1[kMlpH], gx[kMlpIn];
-#pragma unroll
-    for (int o = 0; o < kMlpOut; ++o) gz[o] = g[o] * a.res[o] * (1.0f - a.res[o]);
-#pragma unroll
-    for (int k = 0; k < kMlpH; ++k) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int o = 0; o < kMlpOut; ++o) acc = fmaf(sW[kOffW3 + o * kMlpH + k], gz[o], acc);
-        gh2[k] = a.h2[k] > 0.0f ? acc : 0.0f;
-    }
-#pragma unroll
-    for (int k = 0; k < kMlpH; ++k) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int o = 0; o < kMlpH; ++o) acc = fmaf(sW[kOffW2 + o * kMlpH + k], gh2[o], acc);
-        gh1[k] = a.h1[k] > 0.0f ? acc : 0.0f;
-    }
-#pragma unroll
-    for (int k = 0; k < kMlpIn; ++k) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int o = 0; o < kMlpH; ++o) acc = fmaf(sW[kOffW1 + o * kMlpIn + k], gh1[o], acc);
-        gx[k] = acc;
-    }
-    if (grad_mlp) {
-#pragma unroll
-        for (int o = 0; o < kMlpOut; ++o) {
-            acc_param(sG, kOffB3 + o, gz[o], lane);
-#pragma unroll
-            for (int k = 0; k < kMlpH; ++k) acc_param(sG, kOffW3 + o * kMlpH + k, gz[o] * a.h2[k], lane);
-        }
-#pragma unroll
-        for (int o = 0; o < kMlpH; ++o) {
-            acc_param(sG, kOffB2 + o, gh2[o], lane);
-#pragma unroll
-            for (int k = 0; k < kMlpH; ++k) acc_param(sG, kOffW2 + o * kMlpH + k, gh2[o] * a.h1[k], lane);
-        }
-#pragma unroll
-        for (int o = 0; o < kMlpH; ++o) {
-            acc_param(sG, kOffB1 + o, gh1[o], lane);
-#pragma unroll
-            for (int k = 0; k < kMlpIn; ++k) acc_param(sG, kOffW1 + o * kMlpIn + k, gh1[o] * x[k], lane);
-        }
+        for (int k = 0; k < kRow; ++k) row[k] = 0.0f;   // contributes nothing to the sums below
     }
     __syncthreads();
-    if (grad_mlp)
-        for (int p = threadIdx.x; p < kNParam; p += blockDim.x)
-            if (sG[p] != 0.0f) atomicAdd(grad_mlp + p, sG[p]);
-
+    // dL/dPhi: per parameter, a dot product over the CTA's rays (one global atomic per
+    // parameter per CTA): W1 <- g1 (x) x, W2 <- g2 (x) h1, W3 <- gz (x) h2, biases <- g.
+    if (grad_mlp) {
+        for (int p = threadIdx.x; p < kNParam; p += blockDim.x) {
+            int a, b;    // row offsets of the two factors; b < 0 for a bias
+            if (p < kOffB1) { a = kRowG1 + p / kMlpIn; b = kRowX + p % kMlpIn; }
+            else if (p < kOffW2) { a = kRowG1 + (p - kOffB1); b = -1; }
+            else if (p < kOffB2) { a = kRowG2 + (p - kOffW2) / kMlpH; b = kRowH1 + (p - kOffW2) % kMlpH; }
+            else if (p < kOffW3) { a = kRowG2 + (p - kOffB2); b = -1; }
+            else if (p < kOffB3) { a = kRowGZ + (p - kOffW3) / kMlpH; b = kRowH2 + (p - kOffW3) % kMlpH; }
+            else { a = kRowGZ + (p - kOffB3); b = -1; }
+            float acc = 0.0f;
+            if (b >= 0) {
+#pragma unroll 4
+                for (int t = 0; t < kBwdThreads; ++t) acc = fmaf(rows[t * kRow + a], rows[t * kRow + b], acc);
+            } else {
+#pragma unroll 4
+                for (int t = 0; t < kBwdThreads; ++t) acc += rows[t * kRow + a];
+            }
+            if (acc != 0.0f) atomicAdd(grad_mlp + p, acc);
+        }
+    }
     if (active && grad_atlas) {
         float gf[7];
 #pragma unroll
@@ -141,8 +177,17 @@ cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_
                                  int64_t n, const float* mlp, const float* grad_rgb, float* grad_atlas,
                                  float* grad_mlp, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((n + 127) / 128);
-    backward_rays_kernel<<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, grad_rgb, grad_atlas, grad_mlp);
+    const size_t smem = backward_smem_bytes();
+    static bool attr_set = false;     // the opt-in for > 48 KB of dynamic shared memory
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(backward_rays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const unsigned grid = (unsigned)((n + kBwdThreads - 1) / kBwdThreads);
+    backward_rays_kernel<<<grid, kBwdThreads, smem, st>>>(s, cams, n_cams, pix, n, mlp, grad_rgb, grad_atlas,
+                                                          grad_mlp);
     return cudaGetLastError();
 }
 
