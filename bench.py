@@ -369,7 +369,55 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
                       "fwd_mrays_s": round(n / (np.mean(ms_f) * 1e-3) / 1e6, 3),
                       "fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3),
                       "ms_fwd": round(float(np.mean(ms_f)), 4), "ms_fwd_bwd": round(float(np.mean(ms_fb)), 4)}
+    del rb, ga, gm
+    if not args.no_large:
+        out["large"] = large_section(args, dev, stream, flush)
     return out
+
+
+def large_section(args, dev, stream, flush):
+    """2048^3 grid: 8 views at 1920x1080 in one persistent launch, then forward and
+    forward+backward over 262,144 seeded rays."""
+    import torch
+    from paper_2103_14645_gb300 import renderer, synth
+    sc = synth.make_scene("shell2048")
+    r = renderer.Renderer.from_scene(sc, dev)
+    mlp = torch.from_numpy(sc.mlp).to(dev)
+    n_pix = sc.n_pixels
+    buf = torch.empty((n_pix, 3), dtype=torch.float32, device=dev)
+    reps = max(3, min(args.steps, 10))
+    dbg = r.render(sc.cameras, mlp, counts=True)
+    cnt = dbg["counts"].double().sum(0).cpu().numpy()
+    alg = 4 * cnt[2] + cnt[0] + 64 * cnt[1] + 12 * n_pix
+    del dbg
+    ms_b = time_steps(lambda: r.render(sc.cameras, mlp, out=buf, persistent=True), reps, 2, stream, flush)
+    del buf
+    pix = torch.from_numpy(sc.extra["pix"]).to(dev)
+    tgt = torch.from_numpy(sc.extra["target"]).to(dev)
+    n = pix.shape[0]
+    ga = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=dev)
+    gm = torch.zeros(883, dtype=torch.float32, device=dev)
+    c = torch.empty((n, 3), dtype=torch.float32, device=dev)
+
+    def fwd():
+        r.render_rays(sc.cameras, pix, mlp, out=c)
+
+    def fwd_bwd():
+        r.render_rays(sc.cameras, pix, mlp, out=c)
+        r.backward(sc.cameras, pix, mlp, c - tgt, ga, gm)
+
+    ms_f = time_steps(fwd, reps, 2, stream, flush)
+    ms_fb = time_steps(fwd_bwd, reps, 2, stream, flush)
+    r.check_status()
+    peak = float(measured_peaks()[0]["hbm_gbs"])
+    t_b = float(np.mean(ms_b))
+    return {"workload": f"shell2048: {sc.N}^3 grid, {sc.B}^3 blocks, {sc.occupancy * 100:.1f}% occupied "
+                        f"({sc.nb} blocks), 8 views at 1920x1080 + {n} backward rays",
+            "batched_fwd_mrays_s": round(n_pix / (t_b * 1e-3) / 1e6, 3),
+            "batched_fwd_ms": round(t_b, 3),
+            "batched_fwd_hbm_frac": round(alg / (t_b * 1e-3) / 1e9 / peak, 4),
+            "rays_fwd_mrays_s": round(n / (np.mean(ms_f) * 1e-3) / 1e6, 3),
+            "rays_fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3)}
 
 
 def cpu_baseline(sc):
@@ -392,6 +440,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2048^3 section")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -129,14 +129,14 @@ def render_image(scene, cam_index: int = 0, mlp=None, val=None):
     return {k: v.reshape(H, W, -1) for k, v in out.items()}
 
 
-def backward_rays(scene, pix, g_rgb, mlp=None, val=None, cams=None):
+def backward_rays(scene, pix, g_rgb, mlp=None, val=None, cams=None, atlas_grad=True):
     """Adjoint for upstream dL/dC g_rgb[n,3]. Returns (grad_val [nb,B,B,B,8] f64 with
-    channel 0 zero, grad_mlp [883] f64)."""
+    channel 0 zero, or None when atlas_grad is False; grad_mlp [883] f64)."""
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 3)
     g = np.ascontiguousarray(g_rgb, np.float64).reshape(-1, 3)
     assert g.shape[0] == pix.shape[0]
     args, keep = _scene_args(scene, val, mlp, cams)
-    grad = np.zeros(scene.atlas.shape, np.float64)
+    grad = np.zeros(scene.atlas.shape, np.float64) if atlas_grad else None
     gmlp = np.zeros(NPARAM, np.float64)
     st = _lib().oracle_backward_rays(*args, _p(pix), pix.shape[0], _p(g), _p(grad), _p(gmlp))
     if st:

@@ -399,7 +399,8 @@ int oracle_render_rays(int32_t N, int32_t B, const float* bmin, float extent, do
 
 /* Adjoint of oracle_render_rays for an upstream gradient g_rgb[n][3] (dL/dC).
  * Accumulates dL/d(decoded value) of channels 1..7 into grad[nb][B^3][8] (channel 0,
- * density, is frozen and left untouched) and dL/d(MLP weights) into gmlp[883]. */
+ * density, is frozen and left untouched; grad may be NULL to skip it) and dL/d(MLP
+ * weights) into gmlp[883]. */
 int oracle_backward_rays(int32_t N, int32_t B, const float* bmin, float extent, double sigma_max, const double* bg,
                          const int32_t* ind, const uint8_t* atlas, const double* val, int64_t nb,
                          const double* mlp, const float* cams, int32_t n_cams, const int32_t* pix, int64_t n,
@@ -433,6 +434,7 @@ int oracle_backward_rays(int32_t N, int32_t B, const float* bmin, float extent, 
             mlp_forward(mlp, x, &mm);
             const double* g = g_rgb + 3 * i;
             mlp_backward(mlp, x, &mm, g, gl, gx);
+            if (!grad) continue;                  /* only dL/dPhi requested */
             double gf[7];
             for (int c = 0; c < 3; ++c) gf[c] = g[c] + gx[c];      /* C = C_d + residual */
             for (int c = 0; c < 4; ++c) gf[3 + c] = gx[3 + c];
