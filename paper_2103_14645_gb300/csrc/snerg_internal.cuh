@@ -14,9 +14,10 @@
 // reproducible bit for bit. Colour arithmetic is ordinary FP32.
 //
 // Device layout (built by snerg_prep.cu inside the caller's workspace):
-//   ind    int32 [G^3]                 indirection, -1 = empty (z, y, x)
-//   bdist  uint8 [G^3]                 Chebyshev distance (in blocks, capped) from each
-//                                      block to the nearest occupied block; 0 = occupied
+//   ind    int32 [G^3]                 indirection (z, y, x): the atlas slot of an occupied
+//                                      block, or -D for an empty one, D >= 1 being the
+//                                      Chebyshev distance (in blocks, capped) to the
+//                                      nearest occupied block -- one load gives both
 //   vskip  uint8 [nb][P^3], P = B + 2  per interior voxel, Chebyshev distance (in voxels)
 //                                      to the nearest voxel of the same block with a
 //                                      non-zero density code; 0 <=> the voxel's own code
@@ -145,15 +146,34 @@ __device__ __forceinline__ int nearest_voxel(float u, int N) {
     return min(max((int)floorf(u), 0), N - 1);
 }
 
-// true iff sample k lies before the ray's exit and its nearest voxel's block lies in
-// the box lo..hi (inclusive, per axis)
-__device__ __forceinline__ bool in_box(const DevScene& s, const Ray& r, int k, const int lo[3], const int hi[3]) {
+// A box of blocks lo..hi (inclusive, per axis) as bounds on the sample position: the
+// nearest voxel j = clamp(floor(u), 0, N-1) has its block in [lo, hi] iff
+// u >= lo*B (no bound if lo*B <= 0, where the clamp applies) and u < (hi+1)*B (no bound
+// if (hi+1)*B >= N). floor(u) >= L <=> u >= L and floor(u) <= H <=> u < H + 1 for
+// integers L, H, so the test is exact.
+struct Box {
+    float lo[3], hi[3];
+};
+
+__device__ __forceinline__ Box make_box(const DevScene& s, const int lo[3], const int hi[3]) {
+    Box bx;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int L = lo[i] * s.B, H = (hi[i] + 1) * s.B;
+        bx.lo[i] = L <= 0 ? -INFINITY : (float)L;
+        bx.hi[i] = H >= s.N ? INFINITY : (float)H;
+    }
+    return bx;
+}
+
+// true iff sample k lies before the ray's exit and its nearest voxel's block is in the box
+__device__ __forceinline__ bool in_box(const Ray& r, int k, const Box& bx) {
     const float t = lattice_t(r, k);
     if (!(t < r.t1)) return false;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const int b = nearest_voxel(lattice_u(r, t, i), s.N) >> s.lgB;
-        if (b < lo[i] || b > hi[i]) return false;
+        const float u = lattice_u(r, t, i);
+        if (!(u >= bx.lo[i] && u < bx.hi[i])) return false;
     }
     return true;
 }
@@ -165,25 +185,26 @@ __device__ __forceinline__ bool in_box(const DevScene& s, const Ray& r, int k, c
 // exact search on the lattice itself.
 __device__ __forceinline__ int box_exit(const DevScene& s, const Ray& r, const float inv_d[3], int k,
                                         const int lo[3], const int hi[3]) {
+    const Box bx = make_box(s, lo, hi);
     float te = r.t1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        if (r.d[i] > 0.0f) te = fminf(te, ((float)((hi[i] + 1) * s.B) - r.o[i]) * inv_d[i]);
-        else if (r.d[i] < 0.0f) te = fminf(te, ((float)(lo[i] * s.B) - r.o[i]) * inv_d[i]);
+        if (r.d[i] > 0.0f) te = fminf(te, (bx.hi[i] - r.o[i]) * inv_d[i]);
+        else if (r.d[i] < 0.0f) te = fminf(te, (bx.lo[i] - r.o[i]) * inv_d[i]);
     }
     const float kf = ceilf(te - r.t0 - 0.5f);
     int ke = (kf > (float)s.kmax) ? s.kmax : (kf < 0.0f ? 0 : (int)kf);
     ke = max(ke, k + 1);
     int lo_k = k, hi_k;
-    if (ke - 1 > k && !in_box(s, r, ke - 1, lo, hi)) {
+    if (ke - 1 > k && !in_box(r, ke - 1, bx)) {
         hi_k = ke - 1;
-    } else if (ke < s.kmax && in_box(s, r, ke, lo, hi)) {
+    } else if (ke < s.kmax && in_box(r, ke, bx)) {
         lo_k = ke;
         int step = 1;
         for (;;) {
             hi_k = lo_k + step;
             if (hi_k >= s.kmax) { hi_k = s.kmax; break; }
-            if (!in_box(s, r, hi_k, lo, hi)) break;
+            if (!in_box(r, hi_k, bx)) break;
             lo_k = hi_k;
             step <<= 1;
         }
@@ -192,13 +213,33 @@ __device__ __forceinline__ int box_exit(const DevScene& s, const Ray& r, const f
     }
     while (hi_k - lo_k > 1) {
         const int mid = (lo_k + hi_k) >> 1;
-        if (in_box(s, r, mid, lo, hi)) lo_k = mid; else hi_k = mid;
+        if (in_box(r, mid, bx)) lo_k = mid; else hi_k = mid;
     }
     return hi_k;
 }
 
+// Byte `byte` of w as a float, exactly: the byte is placed in the low mantissa bits of
+// 2^23 (bit pattern 0x4B0000bb) and 2^23 is subtracted. Two full-rate integer/FP ops
+// instead of an integer-to-float conversion.
 __device__ __forceinline__ float code(uint32_t w, int byte) {
-    return (float)((w >> (8 * byte)) & 0xffu);
+    return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7540u | (unsigned)byte)) - 8388608.0f;
+}
+
+// colour/feature accumulation of one composited sample: acc += w_k * trilinear(codes)
+__device__ __forceinline__ void accumulate_colour(MarchState& st, const uint2 cv[8], float wk, const float f[3],
+                                                  const float g[3]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float tw = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
+        const float w = wk * tw;
+        st.acc[0] += w * code(cv[c].x, 1);
+        st.acc[1] += w * code(cv[c].x, 2);
+        st.acc[2] += w * code(cv[c].x, 3);
+        st.acc[3] += w * code(cv[c].y, 0);
+        st.acc[4] += w * code(cv[c].y, 1);
+        st.acc[5] += w * code(cv[c].y, 2);
+        st.acc[6] += w * code(cv[c].y, 3);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -223,10 +264,11 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
 #pragma unroll
     for (int i = 0; i < 3; ++i) inv_d[i] = __fdividef(1.0f, r.d[i]);
     int k = 0;
+    bool done = false;
     for (;;) {
-        if (k >= s.kmax) { st.limit = true; return; }
+        if (k >= s.kmax) { st.limit = true; break; }
         const float t = lattice_t(r, k);
-        if (!(t < r.t1)) return;
+        if (!(t < r.t1)) break;
         int b[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) b[i] = nearest_voxel(lattice_u(r, t, i), N) >> s.lgB;
@@ -235,7 +277,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
         st.blocks++;
         if (slot < 0) {
             // every block within Chebyshev distance D-1 of b is empty: leave that box
-            const int D1 = (int)__ldg(s.bdist + bi) - 1;
+            const int D1 = -slot - 1;
             const int lo[3] = {b[0] - D1, b[1] - D1, b[2] - D1};
             const int hi[3] = {b[0] + D1, b[1] + D1, b[2] + D1};
             k = box_exit(s, r, inv_d, k, lo, hi);
@@ -308,22 +350,12 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             const float e = expf(-od);
             const float wk = st.T * (1.0f - e);
             st.T *= e;
-            float tw[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                tw[c] = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float w = wk * tw[c];
-                st.acc[0] += w * code(cv[c].x, 1);
-                st.acc[1] += w * code(cv[c].x, 2);
-                st.acc[2] += w * code(cv[c].x, 3);
-                st.acc[3] += w * code(cv[c].y, 0);
-                st.acc[4] += w * code(cv[c].y, 1);
-                st.acc[5] += w * code(cv[c].y, 2);
-                st.acc[6] += w * code(cv[c].y, 3);
-            }
+            accumulate_colour(st, cv, wk, f, g);
             if (GRAD) {
+                float tw[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    tw[c] = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
                 const int B3 = B * B * B;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
@@ -343,10 +375,12 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             }
             if (st.tau > s.taumax) {
                 st.steps += kk - k + 1;
-                return;
+                done = true;
+                break;
             }
             ++kk;
         }
+        if (done) break;
         st.steps += kx - k;
         k = kx;
     }
@@ -556,6 +590,7 @@ cudaError_t launch_build_padded(const int32_t* ind, const int32_t* blk_of_slot, 
 // block level over the G^3 indirection grid, voxel level inside each stored block.
 cudaError_t launch_block_distance(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
                                   uint8_t* bdist, cudaStream_t st);
+cudaError_t launch_encode_distance(int32_t* ind, const uint8_t* bdist, int64_t n, cudaStream_t st);
 cudaError_t launch_voxel_distance(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
                                   uint8_t* vskip, cudaStream_t st);
 

@@ -121,6 +121,12 @@ __global__ void dt_pass_z_padded_kernel(const uint8_t* __restrict__ in, uint8_t*
     }
 }
 
+// ind[i] < 0 (empty) becomes -bdist[i] (>= 1): the march reads one word per block
+__global__ void encode_distance_kernel(int32_t* __restrict__ ind, const uint8_t* __restrict__ bdist, int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        if (ind[t] < 0) ind[t] = -(int32_t)max((int)bdist[t], 1);
+}
+
 static unsigned grid_for(int64_t n) {
     const int64_t b = (n + 255) / 256;
     return (unsigned)(b < 1048576 ? (b > 0 ? b : 1) : 1048576);
@@ -166,4 +172,12 @@ cudaError_t launch_build_padded(const int32_t* ind, const int32_t* blk_of_slot, 
     return cudaGetLastError();
 }
 
+}  // namespace snerg
+
+namespace snerg {
+cudaError_t launch_encode_distance(int32_t* ind, const uint8_t* bdist, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    encode_distance_kernel<<<grid_for(n), 256, 0, st>>>(ind, bdist, n);
+    return cudaGetLastError();
+}
 }  // namespace snerg
