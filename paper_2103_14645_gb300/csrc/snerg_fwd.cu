@@ -12,10 +12,9 @@ __global__ void __launch_bounds__(128, 8) render_image_kernel(const DevScene s, 
                                                            const float* __restrict__ mlp,
                                                            float* __restrict__ rgb, const DebugOut dbg) {
     __shared__ __align__(16) float sW[kNParam + 1];
-    __shared__ float sX[128 * kXStride];
     load_mlp_smem_t(sW, mlp);
     __syncthreads();
-    float* xrow = sX + threadIdx.x * kXStride;
+    float* xrow = nullptr;     // the MLP reads its inputs from registers
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
@@ -51,10 +50,9 @@ __global__ void __launch_bounds__(128, 8) render_rays_kernel(const DevScene s, c
                                                           int64_t n, const float* __restrict__ mlp,
                                                           float* __restrict__ rgb, const DebugOut dbg) {
     __shared__ __align__(16) float sW[kNParam + 1];
-    __shared__ float sX[128 * kXStride];
     load_mlp_smem_t(sW, mlp);
     __syncthreads();
-    float* xrow = sX + threadIdx.x * kXStride;
+    float* xrow = nullptr;     // the MLP reads its inputs from registers
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int ci = __ldg(pix + 3 * i), px = __ldg(pix + 3 * i + 1), py = __ldg(pix + 3 * i + 2);
@@ -99,10 +97,9 @@ __global__ void __launch_bounds__(128, 8) render_persistent_kernel(const DevScen
                                                                 float* __restrict__ rgb,
                                                                 int32_t* __restrict__ queue) {
     __shared__ __align__(16) float sW[kNParam + 1];
-    __shared__ float sX[128 * kXStride];
     load_mlp_smem_t(sW, mlp);
     __syncthreads();
-    float* xrow = sX + threadIdx.x * kXStride;
+    float* xrow = nullptr;     // the MLP reads its inputs from registers
     const int lane = threadIdx.x & 31;
     const int passes_x = p.tile_w / p.warp_w;
     const int passes = passes_x * (p.tile_h / p.warp_h);

@@ -533,9 +533,54 @@ __device__ __forceinline__ void mlp_residual(const float* sW, const float* xrow,
     }
 }
 
+// The same MLP with its 34 inputs taken from registers: C_d, V and d directly, the
+// direction encoding generated in order (one sincosf per axis, double-angle identities
+// for the higher octaves) and consumed as produced. Needs no shared-memory row.
+__device__ __forceinline__ void mlp_residual_regs(const float* sW, const float cd[3], const float v[4],
+                                                  const float d[3], float res[3]) {
+    float h[16];
+    load16(h, sW + kOffB1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) fma16(h, sW + kOffW1 + i * kMlpH, cd[i]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) fma16(h, sW + kOffW1 + (3 + i) * kMlpH, v[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) fma16(h, sW + kOffW1 + (7 + i) * kMlpH, d[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float sv, cv;
+        sincosf(d[i], &sv, &cv);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            fma16(h, sW + kOffW1 + (10 + 6 * l + i) * kMlpH, sv);
+            fma16(h, sW + kOffW1 + (13 + 6 * l + i) * kMlpH, cv);
+            const float s2 = 2.0f * sv * cv;          // sin 2a
+            const float c2 = (cv - sv) * (cv + sv);   // cos 2a
+            sv = s2;
+            cv = c2;
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < 16; ++o) h[o] = fmaxf(h[o], 0.0f);
+    float h2[16];
+    load16(h2, sW + kOffB2);
+#pragma unroll
+    for (int i = 0; i < kMlpH; ++i) fma16(h2, sW + kOffW2 + i * kMlpH, h[i]);
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) {
+        float w3[16];
+        load16(w3, sW + kOffW3 + o * kMlpH);
+        float acc = sW[kOffB3 + o];
+#pragma unroll
+        for (int i = 0; i < kMlpH; ++i) acc = fmaf(w3[i], fmaxf(h2[i], 0.0f), acc);
+        res[o] = 1.0f / (1.0f + expf(-acc));
+    }
+}
+
 // Finish one ray: colour = C_d + residual + T bg (residual only if something was
-// composited). xrow: this thread's kXStride-float row of shared memory; sW: weights in
-// the transposed layout of load_mlp_smem_t.
+// composited). sW: weights in the transposed layout of load_mlp_smem_t; xrow: this
+// thread's kXStride-float row of shared memory to stage the MLP input in, or nullptr to
+// evaluate the MLP from registers.
 __device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, float* xrow, const Ray& r,
                                            const MarchState& st, float rgb[3], float aux[kAuxCh]) {
     const float inv255 = 1.0f / 255.0f;
@@ -546,9 +591,13 @@ __device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, f
     for (int c = 0; c < 4; ++c) v[c] = st.acc[3 + c] * inv255;
     float res[3] = {0.0f, 0.0f, 0.0f};
     if (st.active > 0) {
-        stage_mlp_input(xrow, cd, v, r.d);
         float m[3];
-        mlp_residual(sW, xrow, m);
+        if (xrow) {
+            stage_mlp_input(xrow, cd, v, r.d);
+            mlp_residual(sW, xrow, m);
+        } else {
+            mlp_residual_regs(sW, cd, v, r.d, m);
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) res[c] = cd[c] + m[c];
     }
