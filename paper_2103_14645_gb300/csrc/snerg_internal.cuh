@@ -286,22 +286,24 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
         const int kx = box_exit(s, r, inv_d, k, b, b);
         const uint8_t* vs = s.vskip + (size_t)slot * s.P3;
         const uint2* pa = s.patlas + (size_t)slot * s.P3;
-        const int ox = (b[0] << s.lgB) - 1, oy = (b[1] << s.lgB) - 1, oz = (b[2] << s.lgB) - 1;
+        // block origin minus one, so that the padded local coordinate is floor(u) - o
+        const float ox = (float)((b[0] << s.lgB) - 1), oy = (float)((b[1] << s.lgB) - 1),
+                    oz = (float)((b[2] << s.lgB) - 1);
+        const float Bf = (float)B, Pf = (float)P;
         int kk = k;
         while (kk < kx) {
             const float tk = lattice_t(r, kk);
             float u[3];
-            int j[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                u[i] = lattice_u(r, tk, i);
-                j[i] = nearest_voxel(u[i], N);
-            }
-            // j lies in block b for every kk < kx (box_exit), i.e. l in [1, B]; the
-            // clamp only guards the address
-            const int lx = min(max(j[0] - ox, 1), B), ly = min(max(j[1] - oy, 1), B),
-                      lz = min(max(j[2] - oz, 1), B);
-            const int vd = __ldg(vs + (lz * P + ly) * P + lx);
+            for (int i = 0; i < 3; ++i) u[i] = lattice_u(r, tk, i);
+            // nearest voxel in padded block coordinates: clamp(floor(u), 0, N-1) - origin + 1
+            // equals clamp(floor(u) - origin + 1, 1, B) for a sample of this block (the
+            // grid clamp only acts on the border blocks, where it coincides with the
+            // block clamp); all values are small integers, exact in binary32
+            const float lx = fminf(fmaxf(floorf(u[0]) - ox, 1.0f), Bf);
+            const float ly = fminf(fmaxf(floorf(u[1]) - oy, 1.0f), Bf);
+            const float lz = fminf(fmaxf(floorf(u[2]) - oz, 1.0f), Bf);
+            const int vd = __ldg(vs + (int)fmaf(fmaf(lz, Pf, ly), Pf, lx));
             if (vd != 0) {
                 // no voxel of this block within Chebyshev distance vd-1 has density; the
                 // next vd-2 samples move at most vd-1 voxels per axis, so skip them
@@ -309,12 +311,11 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 continue;
             }
             if (TRACE && st.active < trace_cap)
-                trace[st.active] = ((uint64_t)j[2] * N + (uint64_t)j[1]) * N + (uint64_t)j[0];
+                trace[st.active] = ((uint64_t)(int)(lz + oz) * N + (uint64_t)(int)(ly + oy)) * N +
+                                   (uint64_t)(int)(lx + ox);
             st.active++;
             // trilinear stencil on the virtual grid, cell-centred
-            float f[3], g[3];
-            int l0[3];
-            float fl[3];
+            float f[3], g[3], fl[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const float x = __fsub_rn(u[i], 0.5f);
@@ -322,10 +323,10 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 f[i] = __fsub_rn(x, fl[i]);
                 g[i] = __fsub_rn(1.0f, f[i]);
             }
-            l0[0] = min(max((int)fl[0] - ox, 0), B);
-            l0[1] = min(max((int)fl[1] - oy, 0), B);
-            l0[2] = min(max((int)fl[2] - oz, 0), B);
-            const uint2* p0 = pa + (l0[2] * P + l0[1]) * P + l0[0];
+            const float l0x = fminf(fmaxf(fl[0] - ox, 0.0f), Bf);
+            const float l0y = fminf(fmaxf(fl[1] - oy, 0.0f), Bf);
+            const float l0z = fminf(fmaxf(fl[2] - oz, 0.0f), Bf);
+            const uint2* p0 = pa + (int)fmaf(fmaf(l0z, Pf, l0y), Pf, l0x);
             const int PP = P * P;
             uint2 cv[8];   // index = z*4 + y*2 + x
             cv[0] = __ldg(p0);
