@@ -113,9 +113,18 @@ snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t* d_indirec
                           const uint8_t* d_atlas, int64_t num_blocks, void* d_workspace,
                           size_t ws_bytes, void* stream, snerg_handle* out);
 
+/* Store view-dependence MLP weights (HOST float32 [SNERG_MLP_PARAMS], flat layout above)
+ * in the handle. Render calls made with d_mlp == NULL then take these weights as a
+ * kernel parameter, so every weight is a constant operand of the kernel's FMAs (the
+ * paper's viewer likewise compiles the network's biases into its shader and keeps the
+ * weights in uniform textures, App. A). Returns SNERG_E_INVAL for non-finite weights. */
+snerg_status snerg_set_mlp(snerg_handle h, const float* mlp);
+
 /* Render every pixel of n_cams cameras (Sec. 5.2 and App. A; Eqs. 2, 5-7).
  *   cams   : HOST array of n_cams (1..SNERG_MAX_CAMERAS) cameras, W, H >= 0.
- *   d_mlp  : float32 [SNERG_MLP_PARAMS] view-dependence MLP weights.
+ *   d_mlp  : float32 [SNERG_MLP_PARAMS] view-dependence MLP weights in device memory,
+ *            or NULL to use the weights stored with snerg_set_mlp (SNERG_E_INVAL if
+ *            none were stored).
  *   d_rgb  : float32 output [total pixels][3] addressed through out_offset.
  *   opts   : nullable. Debug outputs (aux, counts, trace) use the plain launch.
  * The colour is C = C_d + sigmoid(MLP(C_d, V, PE(d))) + T bg if any sample was
@@ -125,7 +134,8 @@ snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, int32_t n_ca
                           void* stream);
 
 /* Render a list of rays: d_pix int32 [n][3] = (camera index, x, y). Output row i of
- * d_rgb (and of the optional opts outputs) belongs to ray i; out_offset is ignored. */
+ * d_rgb (and of the optional opts outputs) belongs to ray i; out_offset is ignored.
+ * d_mlp as for snerg_render (NULL = the snerg_set_mlp weights). */
 snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
                                const int32_t* d_pix, int64_t n, const float* d_mlp,
                                float* d_rgb, const snerg_render_opts* opts, void* stream);

@@ -107,8 +107,10 @@ struct snerg_scene {
     int num_sms = 1;
     cudaStream_t cap_stream = nullptr;
     std::map<std::vector<int32_t>, PersistentConfig> tuned;   // key: camera sizes
-    std::map<PersistentConfig, GraphEntry> graphs;
+    std::map<std::pair<PersistentConfig, bool>, GraphEntry> graphs;   // key: shape, weights-as-parameters
     PersistentConfig last{0, 0, 0, 0, 0};
+    MlpWeights host_w;        // snerg_set_mlp: weights in the transposed kernel layout
+    bool has_w = false;
 };
 
 extern "C" size_t snerg_workspace_bytes(const snerg_scene_desc* desc, int64_t num_blocks) {
@@ -238,16 +240,16 @@ static void fill_params(PersistentParams& p, const snerg_camera* cams, int32_t n
 }
 
 static cudaError_t launch_persistent_direct(snerg_scene* h, const PersistentParams& p, const PersistentConfig& c,
-                                            const float* mlp, float* rgb, cudaStream_t st) {
+                                            const float* mlp, const MlpWeights* pw, float* rgb, cudaStream_t st) {
     int32_t* queue = h->hdr + kHdrQueue;
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     h->launches++;
-    return launch_render_persistent(h->ds, p, mlp, rgb, queue, h->num_sms * c.ctas_per_sm, c.block, st);
+    return launch_render_persistent(h->ds, p, mlp, pw, rgb, queue, h->num_sms * c.ctas_per_sm, c.block, st);
 }
 
-static PersistentConfig autotune(snerg_scene* h, const snerg_camera* cams, int32_t n, const float* mlp, float* rgb,
-                                 cudaStream_t st) {
+static PersistentConfig autotune(snerg_scene* h, const snerg_camera* cams, int32_t n, const float* mlp,
+                                 const MlpWeights* pw, float* rgb, cudaStream_t st) {
     static const int shapes[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
     static const int passes[2] = {1, 4};
     static const int ctas[2] = {4, 8};
@@ -263,9 +265,9 @@ static PersistentConfig autotune(snerg_scene* h, const snerg_camera* cams, int32
     PersistentParams* p = new PersistentParams;
     for (const auto& c : cand) {
         fill_params(*p, cams, n, c);
-        if (launch_persistent_direct(h, *p, c, mlp, rgb, st) != cudaSuccess) continue;   // warm-up
+        if (launch_persistent_direct(h, *p, c, mlp, pw, rgb, st) != cudaSuccess) continue;   // warm-up
         cudaEventRecord(e0, st);
-        if (launch_persistent_direct(h, *p, c, mlp, rgb, st) != cudaSuccess) continue;
+        if (launch_persistent_direct(h, *p, c, mlp, pw, rgb, st) != cudaSuccess) continue;
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.0f;
@@ -282,7 +284,7 @@ static PersistentConfig autotune(snerg_scene* h, const snerg_camera* cams, int32
 }
 
 static snerg_status render_persistent(snerg_scene* h, const snerg_camera* cams, int32_t n, const float* mlp,
-                                      float* rgb, const snerg_render_opts* o, cudaStream_t st) {
+                                      const MlpWeights* pw, float* rgb, const snerg_render_opts* o, cudaStream_t st) {
     PersistentConfig cfg{0, 0, 0, 128, 0};
     const bool manual = o && o->tile_w > 0 && o->tile_h > 0 && o->ctas_per_sm > 0;
     if (manual) {
@@ -300,7 +302,7 @@ static snerg_status render_persistent(snerg_scene* h, const snerg_camera* cams, 
             key.push_back(cams[i].H);
         }
         auto it = h->tuned.find(key);
-        if (it == h->tuned.end()) it = h->tuned.emplace(key, autotune(h, cams, n, mlp, rgb, st)).first;
+        if (it == h->tuned.end()) it = h->tuned.emplace(key, autotune(h, cams, n, mlp, pw, rgb, st)).first;
         cfg = it->second;
     }
     h->last = cfg;
@@ -309,14 +311,15 @@ static snerg_status render_persistent(snerg_scene* h, const snerg_camera* cams, 
     fill_params(*p, cams, n, cfg);
     const int grid = h->num_sms * cfg.ctas_per_sm;
     int32_t* queue = h->hdr + kHdrQueue;
-    GraphEntry& ge = h->graphs[cfg];
+    const auto gkey = std::make_pair(cfg, pw != nullptr);
+    GraphEntry& ge = h->graphs[gkey];
     cudaError_t e = cudaSuccess;
     if (!ge.exec) {
         if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaMemsetAsync(queue, 0, sizeof(int32_t), h->cap_stream);
-            launch_render_persistent(h->ds, *p, mlp, rgb, queue, grid, cfg.block, h->cap_stream);
+            launch_render_persistent(h->ds, *p, mlp, pw, rgb, queue, grid, cfg.block, h->cap_stream);
             e = cudaStreamEndCapture(h->cap_stream, &ge.graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
@@ -335,7 +338,7 @@ static snerg_status render_persistent(snerg_scene* h, const snerg_camera* cams, 
         if (e != cudaSuccess) {
             if (ge.exec) cudaGraphExecDestroy(ge.exec);
             if (ge.graph) cudaGraphDestroy(ge.graph);
-            h->graphs.erase(cfg);
+            h->graphs.erase(gkey);
             delete p;
             return SNERG_E_CUDA;
         }
@@ -344,10 +347,12 @@ static snerg_status render_persistent(snerg_scene* h, const snerg_camera* cams, 
     DevScene ds = h->ds;
     const float* mlp_arg = mlp;
     float* rgb_arg = rgb;
-    void* args[] = {(void*)&ds, (void*)p, (void*)&mlp_arg, (void*)&rgb_arg, (void*)&queue};
+    static const MlpWeights zero_w = {};
+    const MlpWeights* w_arg = pw ? pw : &zero_w;
+    void* args[] = {(void*)&ds, (void*)p, (void*)&mlp_arg, (void*)w_arg, (void*)&rgb_arg, (void*)&queue};
     cudaKernelNodeParams kp;
     std::memset(&kp, 0, sizeof(kp));
-    kp.func = const_cast<void*>(persistent_kernel_fn());
+    kp.func = const_cast<void*>(persistent_kernel_fn(pw != nullptr));
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(cfg.block);
     kp.sharedMemBytes = 0;
@@ -369,13 +374,15 @@ extern "C" snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, i
         pixels += (int64_t)cams[i].W * cams[i].H;
     }
     if (pixels == 0) return SNERG_OK;
-    if (!d_mlp || !d_rgb) return SNERG_E_INVAL;
+    if (!d_rgb || (!d_mlp && !h->has_w)) return SNERG_E_INVAL;
+    const MlpWeights* pw = d_mlp ? nullptr : &h->host_w;
     cudaStream_t st = (cudaStream_t)stream;
-    if (opts && opts->persistent && !opts_debug(opts)) return render_persistent(h, cams, n_cams, d_mlp, d_rgb, opts, st);
+    if (opts && opts->persistent && !opts_debug(opts))
+        return render_persistent(h, cams, n_cams, d_mlp, pw, d_rgb, opts, st);
     const DebugOut dbg = make_dbg(opts);
     for (int i = 0; i < n_cams; ++i) {
         if (cams[i].W == 0 || cams[i].H == 0) continue;
-        cudaError_t e = launch_render_image(h->ds, cams[i], d_mlp, d_rgb, dbg, st);
+        cudaError_t e = launch_render_image(h->ds, cams[i], d_mlp, pw, d_rgb, dbg, st);
         if (e != cudaSuccess) return SNERG_E_CUDA;
         h->launches++;
     }
@@ -400,8 +407,9 @@ extern "C" snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* ca
     if (!t) return SNERG_E_NOMEM;
     if (!make_table(cams, n_cams, t)) { delete t; return SNERG_E_INVAL; }
     if (n == 0) { delete t; return SNERG_OK; }
-    if (!d_pix || !d_mlp || !d_rgb) { delete t; return SNERG_E_INVAL; }
-    cudaError_t e = launch_render_rays(h->ds, *t, n_cams, d_pix, n, d_mlp, d_rgb, make_dbg(opts), (cudaStream_t)stream);
+    if (!d_pix || !d_rgb || (!d_mlp && !h->has_w)) { delete t; return SNERG_E_INVAL; }
+    cudaError_t e = launch_render_rays(h->ds, *t, n_cams, d_pix, n, d_mlp, d_mlp ? nullptr : &h->host_w, d_rgb,
+                                       make_dbg(opts), (cudaStream_t)stream);
     delete t;
     if (e != cudaSuccess) return SNERG_E_CUDA;
     h->launches++;
@@ -437,6 +445,25 @@ extern "C" snerg_status snerg_last_status(snerg_handle h, void* stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return SNERG_E_CUDA;
     return (snerg_status)v;
+}
+
+extern "C" snerg_status snerg_set_mlp(snerg_handle h, const float* mlp) {
+    if (!h || !mlp) return SNERG_E_INVAL;
+    MlpWeights w;
+    std::memset(&w, 0, sizeof(w));
+    for (int i = 0; i < kNParam; ++i) {
+        if (!std::isfinite(mlp[i])) return SNERG_E_INVAL;
+        int dst = i;
+        if (i < kOffB1) {                              // W1[o][k] -> W1^T[k][o]
+            dst = kOffW1 + (i % kMlpIn) * kMlpH + i / kMlpIn;
+        } else if (i >= kOffW2 && i < kOffB2) {        // W2[o][k] -> W2^T[k][o]
+            dst = kOffW2 + ((i - kOffW2) % kMlpH) * kMlpH + (i - kOffW2) / kMlpH;
+        }
+        w.w[dst] = mlp[i];
+    }
+    h->host_w = w;
+    h->has_w = true;
+    return SNERG_OK;
 }
 
 extern "C" int64_t snerg_launch_count(snerg_handle h) { return h ? h->launches : 0; }

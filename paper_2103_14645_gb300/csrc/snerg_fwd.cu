@@ -1,20 +1,27 @@
 // snerg_fwd.cu -- forward render kernels: one camera per launch, ray lists, and the
 // persistent multi-camera kernel that drains a (camera, tile) work queue.
 // The per-ray arithmetic is in snerg_internal.cuh (Sec. 5.2, App. A; Eqs. 2, 5-7).
+//
+// Every kernel comes in two flavours for the view-dependence MLP (Eq. 7): PW = true
+// reads the weights from the kernel parameter `pw` (constant-bank operands; set with
+// snerg_set_mlp), PW = false stages them from device memory into shared memory (the
+// form the autograd path uses, where the weights live in a tensor).
 #include "snerg_internal.cuh"
 
 namespace snerg {
 
 // Warp w of a 128-thread CTA covers an 8x4 pixel packet of the CTA's 16x8 tile, so the
 // 32 rays of a warp are neighbours on screen and walk neighbouring voxels together.
-template <bool DBG>
+template <bool DBG, bool PW>
 __global__ void __launch_bounds__(128, 8) render_image_kernel(const DevScene s, const snerg_camera cam,
-                                                           const float* __restrict__ mlp,
-                                                           float* __restrict__ rgb, const DebugOut dbg) {
-    __shared__ __align__(16) float sW[kNParam + 1];
-    load_mlp_smem_t(sW, mlp);
-    __syncthreads();
-    float* xrow = nullptr;     // the MLP reads its inputs from registers
+                                                              const float* __restrict__ mlp,
+                                                              const __grid_constant__ MlpWeights pw,
+                                                              float* __restrict__ rgb, const DebugOut dbg) {
+    __shared__ __align__(16) float sW[PW ? 4 : kNParam + 1];
+    if (!PW) {
+        load_mlp_smem_t(sW, mlp);
+        __syncthreads();
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
@@ -28,7 +35,7 @@ __global__ void __launch_bounds__(128, 8) render_image_kernel(const DevScene s, 
         march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
     record_status(s, st);
     float c[3], aux[kAuxCh];
-    finish_ray(s, sW, xrow, r, st, c, aux);
+    finish_ray(s, sW, nullptr, r, st, c, aux, PW ? &pw : nullptr);
     rgb[pix * 3 + 0] = c[0];
     rgb[pix * 3 + 1] = c[1];
     rgb[pix * 3 + 2] = c[2];
@@ -44,15 +51,17 @@ __global__ void __launch_bounds__(128, 8) render_image_kernel(const DevScene s, 
     }
 }
 
-template <bool DBG>
+template <bool DBG, bool PW>
 __global__ void __launch_bounds__(128, 8) render_rays_kernel(const DevScene s, const __grid_constant__ CamTable cams,
-                                                          int32_t n_cams, const int32_t* __restrict__ pix,
-                                                          int64_t n, const float* __restrict__ mlp,
-                                                          float* __restrict__ rgb, const DebugOut dbg) {
-    __shared__ __align__(16) float sW[kNParam + 1];
-    load_mlp_smem_t(sW, mlp);
-    __syncthreads();
-    float* xrow = nullptr;     // the MLP reads its inputs from registers
+                                                             int32_t n_cams, const int32_t* __restrict__ pix,
+                                                             int64_t n, const float* __restrict__ mlp,
+                                                             const __grid_constant__ MlpWeights pw,
+                                                             float* __restrict__ rgb, const DebugOut dbg) {
+    __shared__ __align__(16) float sW[PW ? 4 : kNParam + 1];
+    if (!PW) {
+        load_mlp_smem_t(sW, mlp);
+        __syncthreads();
+    }
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int ci = __ldg(pix + 3 * i), px = __ldg(pix + 3 * i + 1), py = __ldg(pix + 3 * i + 2);
@@ -71,7 +80,7 @@ __global__ void __launch_bounds__(128, 8) render_rays_kernel(const DevScene s, c
         march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
     record_status(s, st);
     float c[3], aux[kAuxCh];
-    finish_ray(s, sW, xrow, r, st, c, aux);
+    finish_ray(s, sW, nullptr, r, st, c, aux, PW ? &pw : nullptr);
     rgb[i * 3 + 0] = c[0];
     rgb[i * 3 + 1] = c[1];
     rgb[i * 3 + 2] = c[2];
@@ -91,15 +100,18 @@ __global__ void __launch_bounds__(128, 8) render_rays_kernel(const DevScene s, c
 // (tile_w x tile_h pixels of one camera) from a global counter until the queue is empty,
 // and renders each item in warp_w x warp_h packets of 32 rays. The counter is zeroed by
 // the launch sequence (a memset node of the captured graph) before every launch.
+template <bool PW>
 __global__ void __launch_bounds__(128, 8) render_persistent_kernel(const DevScene s,
-                                                                const __grid_constant__ PersistentParams p,
-                                                                const float* __restrict__ mlp,
-                                                                float* __restrict__ rgb,
-                                                                int32_t* __restrict__ queue) {
-    __shared__ __align__(16) float sW[kNParam + 1];
-    load_mlp_smem_t(sW, mlp);
-    __syncthreads();
-    float* xrow = nullptr;     // the MLP reads its inputs from registers
+                                                                   const __grid_constant__ PersistentParams p,
+                                                                   const float* __restrict__ mlp,
+                                                                   const __grid_constant__ MlpWeights pw,
+                                                                   float* __restrict__ rgb,
+                                                                   int32_t* __restrict__ queue) {
+    __shared__ __align__(16) float sW[PW ? 4 : kNParam + 1];
+    if (!PW) {
+        load_mlp_smem_t(sW, mlp);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int passes_x = p.tile_w / p.warp_w;
     const int passes = passes_x * (p.tile_h / p.warp_h);
@@ -126,7 +138,7 @@ __global__ void __launch_bounds__(128, 8) render_persistent_kernel(const DevScen
                 march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
                 record_status(s, st);
                 float c[3], aux[kAuxCh];
-                finish_ray(s, sW, xrow, r, st, c, aux);
+                finish_ray(s, sW, nullptr, r, st, c, aux, PW ? &pw : nullptr);
                 const int64_t o = (cam.out_offset + (int64_t)py * cam.W + px) * 3;
                 rgb[o + 0] = c[0];
                 rgb[o + 1] = c[1];
@@ -136,32 +148,54 @@ __global__ void __launch_bounds__(128, 8) render_persistent_kernel(const DevScen
     }
 }
 
-cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, float* rgb,
-                                const DebugOut& dbg, cudaStream_t st) {
+static const MlpWeights& no_weights() {
+    static const MlpWeights z = {};
+    return z;
+}
+
+cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
+                                float* rgb, const DebugOut& dbg, cudaStream_t st) {
     if (cam.W <= 0 || cam.H <= 0) return cudaSuccess;
     dim3 grid((cam.W + 15) / 16, (cam.H + 7) / 8);
     const bool d = dbg.aux || dbg.counts || dbg.trace;
-    if (d) render_image_kernel<true><<<grid, 128, 0, st>>>(s, cam, mlp, rgb, dbg);
-    else render_image_kernel<false><<<grid, 128, 0, st>>>(s, cam, mlp, rgb, dbg);
+    const MlpWeights& w = pw ? *pw : no_weights();
+    if (pw) {
+        if (d) render_image_kernel<true, true><<<grid, 128, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        else render_image_kernel<false, true><<<grid, 128, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+    } else {
+        if (d) render_image_kernel<true, false><<<grid, 128, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        else render_image_kernel<false, false><<<grid, 128, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
-                               int64_t n, const float* mlp, float* rgb, const DebugOut& dbg, cudaStream_t st) {
+                               int64_t n, const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg,
+                               cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)((n + 127) / 128);
     const bool d = dbg.aux || dbg.counts || dbg.trace;
-    if (d) render_rays_kernel<true><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, rgb, dbg);
-    else render_rays_kernel<false><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, rgb, dbg);
+    const MlpWeights& w = pw ? *pw : no_weights();
+    if (pw) {
+        if (d) render_rays_kernel<true, true><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
+        else render_rays_kernel<false, true><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
+    } else {
+        if (d) render_rays_kernel<true, false><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
+        else render_rays_kernel<false, false><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_render_persistent(const DevScene& s, const PersistentParams& p, const float* mlp, float* rgb,
-                                     int32_t* queue, int grid, int block, cudaStream_t st) {
-    render_persistent_kernel<<<grid, block, 0, st>>>(s, p, mlp, rgb, queue);
+cudaError_t launch_render_persistent(const DevScene& s, const PersistentParams& p, const float* mlp,
+                                     const MlpWeights* pw, float* rgb, int32_t* queue, int grid, int block,
+                                     cudaStream_t st) {
+    if (pw) render_persistent_kernel<true><<<grid, block, 0, st>>>(s, p, mlp, *pw, rgb, queue);
+    else render_persistent_kernel<false><<<grid, block, 0, st>>>(s, p, mlp, no_weights(), rgb, queue);
     return cudaGetLastError();
 }
 
-const void* persistent_kernel_fn() { return (const void*)render_persistent_kernel; }
+const void* persistent_kernel_fn(bool param_weights) {
+    return param_weights ? (const void*)render_persistent_kernel<true> : (const void*)render_persistent_kernel<false>;
+}
 
 }  // namespace snerg

@@ -578,12 +578,66 @@ __device__ __forceinline__ void mlp_residual_regs(const float* sW, const float c
     }
 }
 
+// Weights in the same transposed layout, passed by value as a kernel parameter (set with
+// snerg_set_mlp). The kernel then reads every weight as a constant-bank operand of its
+// FMA: no load, no latency, no registers -- the GPU counterpart of the paper's viewer,
+// whose shader has the network biases compiled in (App. A).
+struct MlpWeights {
+    float w[kNParam + 1];
+};
+
+__device__ __forceinline__ void mlp_residual_param(const MlpWeights& W, const float cd[3], const float v[4],
+                                                   const float d[3], float res[3]) {
+    float h[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) h[o] = W.w[kOffB1 + o];
+    float x[10] = {cd[0], cd[1], cd[2], v[0], v[1], v[2], v[3], d[0], d[1], d[2]};
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+#pragma unroll
+        for (int o = 0; o < 16; ++o) h[o] = fmaf(W.w[kOffW1 + i * kMlpH + o], x[i], h[o]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float sv, cv;
+        sincosf(d[i], &sv, &cv);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+#pragma unroll
+            for (int o = 0; o < 16; ++o) {
+                h[o] = fmaf(W.w[kOffW1 + (10 + 6 * l + i) * kMlpH + o], sv, h[o]);
+                h[o] = fmaf(W.w[kOffW1 + (13 + 6 * l + i) * kMlpH + o], cv, h[o]);
+            }
+            const float s2 = 2.0f * sv * cv;          // sin 2a
+            const float c2 = (cv - sv) * (cv + sv);   // cos 2a
+            sv = s2;
+            cv = c2;
+        }
+    }
+    float h2[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) h2[o] = W.w[kOffB2 + o];
+#pragma unroll
+    for (int i = 0; i < kMlpH; ++i) {
+        const float hi = fmaxf(h[i], 0.0f);
+#pragma unroll
+        for (int o = 0; o < 16; ++o) h2[o] = fmaf(W.w[kOffW2 + i * kMlpH + o], hi, h2[o]);
+    }
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) {
+        float acc = W.w[kOffB3 + o];
+#pragma unroll
+        for (int i = 0; i < kMlpH; ++i) acc = fmaf(W.w[kOffW3 + o * kMlpH + i], fmaxf(h2[i], 0.0f), acc);
+        res[o] = 1.0f / (1.0f + expf(-acc));
+    }
+}
+
 // Finish one ray: colour = C_d + residual + T bg (residual only if something was
 // composited). sW: weights in the transposed layout of load_mlp_smem_t; xrow: this
 // thread's kXStride-float row of shared memory to stage the MLP input in, or nullptr to
 // evaluate the MLP from registers.
 __device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, float* xrow, const Ray& r,
-                                           const MarchState& st, float rgb[3], float aux[kAuxCh]) {
+                                           const MarchState& st, float rgb[3], float aux[kAuxCh],
+                                           const MlpWeights* pw = nullptr) {
     const float inv255 = 1.0f / 255.0f;
     float cd[3], v[4];
 #pragma unroll
@@ -593,7 +647,9 @@ __device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, f
     float res[3] = {0.0f, 0.0f, 0.0f};
     if (st.active > 0) {
         float m[3];
-        if (xrow) {
+        if (pw) {
+            mlp_residual_param(*pw, cd, v, r.d, m);
+        } else if (xrow) {
             stage_mlp_input(xrow, cd, v, r.d);
             mlp_residual(sW, xrow, m);
         } else {
@@ -625,10 +681,12 @@ struct DebugOut {
     int32_t trace_cap;
 };
 
-cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, float* rgb,
-                                const DebugOut& dbg, cudaStream_t st);
+// pw: weights as a kernel parameter (nullptr: read them from `mlp` in device memory)
+cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
+                                float* rgb, const DebugOut& dbg, cudaStream_t st);
 cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
-                               int64_t n, const float* mlp, float* rgb, const DebugOut& dbg, cudaStream_t st);
+                               int64_t n, const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg,
+                               cudaStream_t st);
 cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
                                  const float* mlp, const float* grad_rgb, float* grad_atlas, float* grad_mlp,
                                  cudaStream_t st);
@@ -654,8 +712,9 @@ struct PersistentParams {
     int32_t warp_w, warp_h;             // pixels per warp pass (warp_w * warp_h == 32)
 };
 
-cudaError_t launch_render_persistent(const DevScene& s, const PersistentParams& p, const float* mlp, float* rgb,
-                                     int32_t* queue, int grid, int block, cudaStream_t st);
-const void* persistent_kernel_fn();
+cudaError_t launch_render_persistent(const DevScene& s, const PersistentParams& p, const float* mlp,
+                                     const MlpWeights* pw, float* rgb, int32_t* queue, int grid, int block,
+                                     cudaStream_t st);
+const void* persistent_kernel_fn(bool param_weights);
 
 }  // namespace snerg

@@ -25,7 +25,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error"
 
 EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_render_rays",
             "snerg_render_backward", "snerg_last_status", "snerg_launch_count",
-            "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc"]
+            "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc",
+            "snerg_set_mlp"]
 
 
 class SnergError(RuntimeError):
@@ -78,6 +79,8 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_destroy.restype = None
     lib.snerg_status_str.argtypes = [ctypes.c_int]
     lib.snerg_status_str.restype = ctypes.c_char_p
+    lib.snerg_set_mlp.argtypes = [P, P]
+    lib.snerg_set_mlp.restype = ctypes.c_int
     lib.snerg_render_rays_noalloc.argtypes = [P, P, P, i64, P, i32, P, i64, P, P, P, P]
     lib.snerg_render_rays_noalloc.restype = ctypes.c_int
     _LIB = lib
@@ -163,6 +166,14 @@ class Renderer:
                "snerg_persistent_config")
         return tw.value, th.value, c.value
 
+    def set_mlp(self, weights):
+        """Store host MLP weights in the handle; renders called with mlp=None use them as
+        kernel parameters (snerg_set_mlp)."""
+        w = np.ascontiguousarray(np.asarray(weights, np.float32).reshape(-1))
+        if w.size != MLP_PARAMS:
+            raise ValueError(f"{MLP_PARAMS} weights expected")
+        _check(self.lib.snerg_set_mlp(self.handle, w.ctypes.data), "snerg_set_mlp")
+
     def check_status(self):
         """Synchronise and raise if a kernel recorded a device-side error."""
         _check(self.lib.snerg_last_status(self.handle, _stream(self.device)), "device status")
@@ -186,12 +197,14 @@ class Renderer:
         o.ctas_per_sm = int(ctas_per_sm)
         return o, out
 
-    def render(self, cams, mlp: torch.Tensor, out: torch.Tensor | None = None, aux=False, counts=False,
+    def render(self, cams, mlp: torch.Tensor | None, out: torch.Tensor | None = None, aux=False, counts=False,
                trace_cap: int = 0, persistent=False, tile=None, ctas_per_sm: int = 0):
         """Render every pixel of the cameras into out [pixels, 3] (packed by out_offset).
+        mlp: device weights, or None for the weights stored with set_mlp.
         Returns out, or a dict with 'rgb' and the requested debug outputs."""
         c = _cams(cams)
-        _require_cuda(mlp, "mlp", torch.float32)
+        if mlp is not None:
+            _require_cuda(mlp, "mlp", torch.float32)
         n_pix = int(max((int(x["out_offset"]) + int(x["W"]) * int(x["H"]) for x in c), default=0))
         if out is None:
             out = torch.empty((n_pix, 3), dtype=torch.float32, device=self.device)
@@ -208,11 +221,12 @@ class Renderer:
             return extra
         return out
 
-    def render_rays(self, cams, pix: torch.Tensor, mlp: torch.Tensor, out=None, aux=False, counts=False,
+    def render_rays(self, cams, pix: torch.Tensor, mlp: torch.Tensor | None, out=None, aux=False, counts=False,
                     trace_cap: int = 0):
         c = _cams(cams)
         _require_cuda(pix, "pix", torch.int32)
-        _require_cuda(mlp, "mlp", torch.float32)
+        if mlp is not None:
+            _require_cuda(mlp, "mlp", torch.float32)
         n = int(pix.shape[0])
         if out is None:
             out = torch.empty((n, 3), dtype=torch.float32, device=self.device)

@@ -371,3 +371,27 @@ def test_paper_scale_2048_batched_forward_and_backward():
     _, rm = oracle.backward_rays(sc, bp, gr, atlas_grad=False)
     assert np.abs(rm).max() > 0
     assert np.abs(gm.cpu().numpy() - rm).max() <= 1e-4 * np.abs(rm).max()
+
+
+def test_parameter_weights_match_device_weights():
+    """snerg_set_mlp + d_mlp = NULL (weights as kernel parameters) renders what the
+    device-weight path renders, for the plain, ray-list and persistent launches."""
+    sc = scene("gauss64")
+    cams = synth.orbit_cameras(np.random.default_rng(12), [(64, 64), (37, 23), (50, 70)], synth.CAM_RADIUS)
+    r = renderer.Renderer.from_scene(sc, DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    with pytest.raises(renderer.SnergError):
+        r.render(cams, None)               # no weights stored yet
+    r.set_mlp(sc.mlp)
+    ref = r.render(cams, w).cpu().numpy()
+    o = oracle_all(sc, cams=cams)
+    for kw in ({}, {"persistent": True, "tile": (8, 4), "ctas_per_sm": 2}):
+        got = r.render(cams, None, **kw).cpu().numpy()
+        r.check_status()
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-6)
+        assert np.abs(got - o["rgb"]).max() <= TOL
+    pix = torch.from_numpy(synth.all_pixels(cams)).to(DEV)
+    got = r.render_rays(cams, pix, None).cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-6)
+    with pytest.raises(renderer.SnergError):
+        r.set_mlp(np.full(883, np.nan, np.float32))
