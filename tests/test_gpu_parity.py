@@ -395,3 +395,69 @@ def test_parameter_weights_match_device_weights():
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-6)
     with pytest.raises(renderer.SnergError):
         r.set_mlp(np.full(883, np.nan, np.float32))
+
+
+# --------------------------------------------------------------------------------------
+# grid shapes and media at the edges of the method
+# --------------------------------------------------------------------------------------
+
+def _gauss_scene(N, B, occ, sigma_vox, seed, sizes, radius=synth.CAM_RADIUS):
+    ind, atl = synth.gauss_grid(N, B, occ, sigma_vox, seed)
+    rng = np.random.default_rng(seed + 50)
+    cams = synth.orbit_cameras(rng, sizes, radius)
+    return synth.custom_scene(N, B, ind, atl, sigma_vox / (synth.WORLD_EXTENT / N), synth.init_mlp(rng), cams)
+
+
+@pytest.mark.parametrize("N,B", [(48, 16), (96, 32), (32, 2), (128, 64)])
+def test_grid_shapes(N, B):
+    """G = N/B not a power of two, the smallest and the largest macroblock edge."""
+    sc = _gauss_scene(N, B, 0.4, 0.8, 3, [(40, 33), (17, 29)])
+    g, _ = gpu_render(sc, aux=True, counts=True, trace_cap=128)
+    o = oracle_all(sc, trace_cap=128)
+    assert o["counts"][:, 1].max() <= 128
+    assert_parity(g, o)
+    assert (o["counts"][:, 1] > 0).any()
+
+
+def test_dense_grid_every_block_stored():
+    """No empty block at all: every block visit is an occupied one."""
+    sc0 = scene("gauss64")
+    ind, atl = helpers.dense_to_blocks(helpers.blocks_to_dense(sc0), sc0.B, keep_empty=True)
+    sc = synth.custom_scene(sc0.N, sc0.B, ind, atl, sc0.sigma_max, sc0.mlp, sc0.cameras)
+    g, _ = gpu_render(sc, aux=True, counts=True, trace_cap=64)
+    assert_parity(g, oracle_all(sc, trace_cap=64))
+
+
+@pytest.mark.parametrize("sigma_vox", [1e-3, 200.0])
+def test_transparent_and_opaque_media(sigma_vox):
+    """Nearly transparent (no ray saturates: every occupied sample is visited) and
+    opaque (the first composited sample ends the ray)."""
+    sc0 = scene("gauss64")
+    sc = synth.custom_scene(sc0.N, sc0.B, sc0.ind, sc0.atlas, sigma_vox / (sc0.extent / sc0.N), sc0.mlp,
+                            sc0.cameras)
+    g, _ = gpu_render(sc, aux=True, counts=True, trace_cap=256)
+    o = oracle_all(sc, trace_cap=256)
+    assert_parity(g, o)
+    if sigma_vox > 1:
+        assert np.median(o["counts"][o["counts"][:, 1] > 0, 1]) <= 2
+
+
+def test_distant_camera_and_boundary_origins():
+    """A camera 60 grid widths away (large t_start: coarse binary32 lattice, so the exact
+    exit search must correct the distance estimate) and cameras whose centres sit on the
+    grid's faces and edges."""
+    sc = scene("gauss64")
+    far = synth.orbit_cameras(np.random.default_rng(31), [(48, 48)], 60.0, fov_deg=2.0)
+    edge = np.concatenate([helpers.axis_camera((-1.0, 0.1, 0.3), W=7, H=5, f=3.0),
+                           helpers.axis_camera((1.0, 1.0, 1.0), W=6, H=6, f=2.0),
+                           helpers.axis_camera((0.3, -0.2, -1.0), W=5, H=5, f=2.0)])
+    cams = np.concatenate([far, edge])
+    off = 0
+    for c in cams:
+        c["out_offset"] = off
+        off += int(c["W"]) * int(c["H"])
+    g, _ = gpu_render(sc, cams=cams, aux=True, counts=True, trace_cap=64)
+    o = oracle_all(sc, cams=cams, trace_cap=64)
+    assert_parity(g, o)
+    n_far = 48 * 48
+    assert (o["counts"][:n_far, 1] > 0).mean() > 0.1
