@@ -10,21 +10,31 @@
 
 namespace snerg {
 
-// Warp w of a 128-thread CTA covers an 8x4 pixel packet of the CTA's 16x8 tile, so the
-// 32 rays of a warp are neighbours on screen and walk neighbouring voxels together.
-template <bool DBG, bool PW>
-__global__ void __launch_bounds__(128, 8) render_image_kernel(const DevScene s, const snerg_camera cam,
-                                                              const float* __restrict__ mlp,
-                                                              const __grid_constant__ MlpWeights pw,
-                                                              float* __restrict__ rgb, const DebugOut dbg) {
+// Each warp covers an 8x4 pixel packet, so its 32 rays are neighbours on screen and walk
+// neighbouring voxels together. A CTA holds NW warps (1: 8x4, 2: 16x4, 4: 16x8 pixels);
+// small CTAs free their SM slot as soon as their own packets are done, which matters
+// because packets on the object take several times longer than background packets.
+template <int NW>
+struct ImageTile {
+    static constexpr int WX = NW >= 2 ? 2 : 1;      // warps across
+    static constexpr int WY = NW >= 4 ? 2 : 1;      // warps down
+    static constexpr int TW = 8 * WX, TH = 4 * WY;  // CTA tile in pixels
+};
+
+template <bool DBG, bool PW, int NW>
+__global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const DevScene s, const snerg_camera cam,
+                                                                        const float* __restrict__ mlp,
+                                                                        const __grid_constant__ MlpWeights pw,
+                                                                        float* __restrict__ rgb, const DebugOut dbg) {
     __shared__ __align__(16) float sW[PW ? 4 : kNParam + 1];
     if (!PW) {
         load_mlp_smem_t(sW, mlp);
         __syncthreads();
     }
+    using T = ImageTile<NW>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    const int px = blockIdx.x * T::TW + (warp % T::WX) * 8 + (lane & 7);
+    const int py = blockIdx.y * T::TH + (warp / T::WX) * 4 + (lane >> 3);
     if (px >= cam.W || py >= cam.H) return;
     const Ray r = make_ray(s, cam, px, py);
     const int64_t pix = cam.out_offset + (int64_t)py * cam.W + px;
@@ -153,18 +163,22 @@ static const MlpWeights& no_weights() {
     return z;
 }
 
+constexpr int kImageWarps = 4;     // warps per CTA of the one-camera launch
+
 cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
                                 float* rgb, const DebugOut& dbg, cudaStream_t st) {
     if (cam.W <= 0 || cam.H <= 0) return cudaSuccess;
-    dim3 grid((cam.W + 15) / 16, (cam.H + 7) / 8);
+    using T = ImageTile<kImageWarps>;
+    dim3 grid((cam.W + T::TW - 1) / T::TW, (cam.H + T::TH - 1) / T::TH);
+    const int nt = 32 * kImageWarps;
     const bool d = dbg.aux || dbg.counts || dbg.trace;
     const MlpWeights& w = pw ? *pw : no_weights();
     if (pw) {
-        if (d) render_image_kernel<true, true><<<grid, 128, 0, st>>>(s, cam, mlp, w, rgb, dbg);
-        else render_image_kernel<false, true><<<grid, 128, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        if (d) render_image_kernel<true, true, kImageWarps><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        else render_image_kernel<false, true, kImageWarps><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
     } else {
-        if (d) render_image_kernel<true, false><<<grid, 128, 0, st>>>(s, cam, mlp, w, rgb, dbg);
-        else render_image_kernel<false, false><<<grid, 128, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        if (d) render_image_kernel<true, false, kImageWarps><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        else render_image_kernel<false, false, kImageWarps><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
     }
     return cudaGetLastError();
 }
