@@ -225,21 +225,39 @@ __device__ __forceinline__ float code(uint32_t w, int byte) {
     return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7540u | (unsigned)byte)) - 8388608.0f;
 }
 
-// colour/feature accumulation of one composited sample: acc += w_k * trilinear(codes)
+// Two bytes as a float pair (one packed subtract for both)
+__device__ __forceinline__ float2 code2(uint32_t w0, int b0, uint32_t w1, int b1) {
+    const float2 m = make_float2(__int_as_float((int)__byte_perm(w0, 0x4B000000u, 0x7540u | (unsigned)b0)),
+                                 __int_as_float((int)__byte_perm(w1, 0x4B000000u, 0x7540u | (unsigned)b1)));
+    return __fadd2_rn(m, make_float2(-8388608.0f, -8388608.0f));
+}
+
+// colour/feature accumulation of one composited sample: acc += w_k * trilinear(codes),
+// corner by corner, channels in packed pairs (each element is the same fused
+// multiply-add as the scalar form, in the same order)
 __device__ __forceinline__ void accumulate_colour(MarchState& st, const uint2 cv[8], float wk, const float f[3],
                                                   const float g[3]) {
+    float2 a01 = make_float2(st.acc[0], st.acc[1]);
+    float2 a23 = make_float2(st.acc[2], st.acc[3]);
+    float2 a45 = make_float2(st.acc[4], st.acc[5]);
+    float a6 = st.acc[6];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const float tw = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
         const float w = wk * tw;
-        st.acc[0] += w * code(cv[c].x, 1);
-        st.acc[1] += w * code(cv[c].x, 2);
-        st.acc[2] += w * code(cv[c].x, 3);
-        st.acc[3] += w * code(cv[c].y, 0);
-        st.acc[4] += w * code(cv[c].y, 1);
-        st.acc[5] += w * code(cv[c].y, 2);
-        st.acc[6] += w * code(cv[c].y, 3);
+        const float2 ww = make_float2(w, w);
+        a01 = __ffma2_rn(code2(cv[c].x, 1, cv[c].x, 2), ww, a01);
+        a23 = __ffma2_rn(code2(cv[c].x, 3, cv[c].y, 0), ww, a23);
+        a45 = __ffma2_rn(code2(cv[c].y, 1, cv[c].y, 2), ww, a45);
+        a6 = fmaf(code(cv[c].y, 3), w, a6);
     }
+    st.acc[0] = a01.x;
+    st.acc[1] = a01.y;
+    st.acc[2] = a23.x;
+    st.acc[3] = a23.y;
+    st.acc[4] = a45.x;
+    st.acc[5] = a45.y;
+    st.acc[6] = a6;
 }
 
 // ---------------------------------------------------------------------------------
@@ -586,48 +604,51 @@ struct MlpWeights {
     float w[kNParam + 1];
 };
 
+// Packed FP32 pairs (sm_100+ f32x2 FMA): two hidden units per instruction.
+__device__ __forceinline__ void fma16_pairs(float2 h[8], const float* w, float x) {
+    const float2 xx = make_float2(x, x);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) h[q] = __ffma2_rn(make_float2(w[2 * q], w[2 * q + 1]), xx, h[q]);
+}
+
 __device__ __forceinline__ void mlp_residual_param(const MlpWeights& W, const float cd[3], const float v[4],
                                                    const float d[3], float res[3]) {
-    float h[16];
+    float2 h[8];
 #pragma unroll
-    for (int o = 0; o < 16; ++o) h[o] = W.w[kOffB1 + o];
-    float x[10] = {cd[0], cd[1], cd[2], v[0], v[1], v[2], v[3], d[0], d[1], d[2]};
+    for (int q = 0; q < 8; ++q) h[q] = make_float2(W.w[kOffB1 + 2 * q], W.w[kOffB1 + 2 * q + 1]);
+    const float x[10] = {cd[0], cd[1], cd[2], v[0], v[1], v[2], v[3], d[0], d[1], d[2]};
 #pragma unroll
-    for (int i = 0; i < 10; ++i)
-#pragma unroll
-        for (int o = 0; o < 16; ++o) h[o] = fmaf(W.w[kOffW1 + i * kMlpH + o], x[i], h[o]);
+    for (int i = 0; i < 10; ++i) fma16_pairs(h, W.w + kOffW1 + i * kMlpH, x[i]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         float sv, cv;
         sincosf(d[i], &sv, &cv);
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-#pragma unroll
-            for (int o = 0; o < 16; ++o) {
-                h[o] = fmaf(W.w[kOffW1 + (10 + 6 * l + i) * kMlpH + o], sv, h[o]);
-                h[o] = fmaf(W.w[kOffW1 + (13 + 6 * l + i) * kMlpH + o], cv, h[o]);
-            }
+            fma16_pairs(h, W.w + kOffW1 + (10 + 6 * l + i) * kMlpH, sv);
+            fma16_pairs(h, W.w + kOffW1 + (13 + 6 * l + i) * kMlpH, cv);
             const float s2 = 2.0f * sv * cv;          // sin 2a
             const float c2 = (cv - sv) * (cv + sv);   // cos 2a
             sv = s2;
             cv = c2;
         }
     }
-    float h2[16];
+    float2 h2[8];
 #pragma unroll
-    for (int o = 0; o < 16; ++o) h2[o] = W.w[kOffB2 + o];
+    for (int q = 0; q < 8; ++q) h2[q] = make_float2(W.w[kOffB2 + 2 * q], W.w[kOffB2 + 2 * q + 1]);
 #pragma unroll
-    for (int i = 0; i < kMlpH; ++i) {
-        const float hi = fmaxf(h[i], 0.0f);
-#pragma unroll
-        for (int o = 0; o < 16; ++o) h2[o] = fmaf(W.w[kOffW2 + i * kMlpH + o], hi, h2[o]);
+    for (int q = 0; q < 8; ++q) {
+        fma16_pairs(h2, W.w + kOffW2 + (2 * q) * kMlpH, fmaxf(h[q].x, 0.0f));
+        fma16_pairs(h2, W.w + kOffW2 + (2 * q + 1) * kMlpH, fmaxf(h[q].y, 0.0f));
     }
 #pragma unroll
     for (int o = 0; o < kMlpOut; ++o) {
-        float acc = W.w[kOffB3 + o];
+        float2 acc = make_float2(W.w[kOffB3 + o], 0.0f);
 #pragma unroll
-        for (int i = 0; i < kMlpH; ++i) acc = fmaf(W.w[kOffW3 + o * kMlpH + i], fmaxf(h2[i], 0.0f), acc);
-        res[o] = 1.0f / (1.0f + expf(-acc));
+        for (int q = 0; q < 8; ++q)
+            acc = __ffma2_rn(make_float2(W.w[kOffW3 + o * kMlpH + 2 * q], W.w[kOffW3 + o * kMlpH + 2 * q + 1]),
+                             make_float2(fmaxf(h2[q].x, 0.0f), fmaxf(h2[q].y, 0.0f)), acc);
+        res[o] = 1.0f / (1.0f + expf(-(acc.x + acc.y)));
     }
 }
 
