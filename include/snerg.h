@@ -45,7 +45,7 @@ typedef enum {
     SNERG_E_INVAL = 1,        /* invalid argument (sizes, pointers, indirection entries) */
     SNERG_E_NOMEM = 2,        /* caller-provided buffer smaller than required */
     SNERG_E_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
-    SNERG_E_STEP_LIMIT = 4,   /* device: a ray exceeded its iteration cap (4N + 16) */
+    SNERG_E_STEP_LIMIT = 4,   /* device: a ray reached its lattice cap (desc.max_steps) */
     SNERG_E_UNSUPPORTED = 5   /* request outside the compiled limits */
 } snerg_status;
 
@@ -60,6 +60,9 @@ typedef struct {
     float extent;       /* world-space edge length, > 0 */
     float sigma_max;    /* density of code 255 (1/world units): sigma = q / 255 * sigma_max */
     float bg[3];        /* background colour, added with weight T_final */
+    int32_t max_steps;  /* cap on the lattice index of a ray; 0 = 4N + 16 (never reached by a
+                           valid ray). A ray reaching the cap stops, keeps what it composited
+                           and records SNERG_E_STEP_LIMIT in the device status word. */
 } snerg_scene_desc;
 
 /* Pinhole camera (Sec. 4.1 r(t) = o + t d). 80 bytes, host memory.

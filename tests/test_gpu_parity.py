@@ -461,3 +461,21 @@ def test_distant_camera_and_boundary_origins():
     assert_parity(g, o)
     n_far = 48 * 48
     assert (o["counts"][:n_far, 1] > 0).mean() > 0.1
+
+
+def test_step_limit_is_reported_and_cleared():
+    """A lattice cap far below the ray length: rays stop at the cap, the device records
+    SNERG_E_STEP_LIMIT, the host reads it once and the word is cleared. No wait, no fault."""
+    sc = scene("gauss64")
+    r = renderer.Renderer.from_scene(sc, DEV, max_steps=5)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    out = r.render(sc.cameras, w, counts=True)
+    with pytest.raises(renderer.SnergError) as e:
+        r.check_status()
+    assert e.value.code == 4
+    r.check_status()
+    assert int(out["counts"][:, 0].max()) <= 5
+    assert torch.isfinite(out["rgb"]).all()
+    full = renderer.Renderer.from_scene(sc, DEV)
+    full.render(sc.cameras, w)
+    full.check_status()

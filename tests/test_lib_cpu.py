@@ -50,7 +50,7 @@ def test_nm_shows_c_linkage(lib):
 
 
 def _desc(N=64, B=8, extent=2.0, sigma=10.0):
-    return renderer.SceneDesc(N, B, (ctypes.c_float * 3)(-1, -1, -1), extent, sigma, (ctypes.c_float * 3)(1, 1, 1))
+    return renderer.SceneDesc(N, B, (ctypes.c_float * 3)(-1, -1, -1), extent, sigma, (ctypes.c_float * 3)(1, 1, 1), 0)
 
 
 def test_workspace_bytes(lib):
@@ -61,8 +61,10 @@ def test_workspace_bytes(lib):
         need = 7 * G ** 3 + 4 * nb + 9 * nb * P ** 3
         assert need <= got <= need + 7 * 256
         assert got % 256 == 0
+    neg = _desc()
+    neg.max_steps = -1
     for bad in [_desc(64, 6), _desc(60, 8), _desc(64, 8, extent=0.0), _desc(64, 8, sigma=float("nan")),
-                _desc(0, 8), _desc(64 * 1024, 8), _desc(8192, 4)]:
+                _desc(0, 8), _desc(64 * 1024, 8), _desc(8192, 4), neg]:
         assert lib.snerg_workspace_bytes(ctypes.byref(bad), 10) == 0
     assert lib.snerg_workspace_bytes(ctypes.byref(_desc()), -1) == 0
     assert lib.snerg_workspace_bytes(None, 1) == 0
@@ -99,6 +101,7 @@ def test_camera_record_layout():
     assert synth.CAMERA_DTYPE.fields["out_offset"][1] == 72
     assert synth.CAMERA_DTYPE.fields["W"][1] == 64
     assert ctypes.sizeof(renderer.RenderOpts) == 48
+    assert ctypes.sizeof(renderer.SceneDesc) == 44
 
 
 def test_no_cpu_fallback_without_library(tmp_path, monkeypatch):
