@@ -115,13 +115,14 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     r.d[0] = r.d[1] = r.d[2] = 0.0f;
     MarchState st;
     st.active = 0;
+    int k_first = 0;
     if (i < n) {
         const int ci = __ldg(pix + 3 * i), px = __ldg(pix + 3 * i + 1), py = __ldg(pix + 3 * i + 2);
         if (ci >= 0 && ci < n_cams && px >= 0 && py >= 0 && px < cams.c[ci].W && py < cams.c[ci].H)
             r = make_ray(s, cams.c[ci], px, py);
         else
             atomicCAS(s.status, 0, (int)SNERG_E_INVAL);
-        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
+        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr, 0, &k_first);
         record_status(s, st);
     }
     const bool active = st.active > 0;
@@ -168,8 +169,10 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
         for (int c = 0; c < 3; ++c) gf[c] = g[c] + gx[c];     // C = C_d + residual
 #pragma unroll
         for (int c = 0; c < 4; ++c) gf[3 + c] = gx[3 + c];
+        // the second pass starts at the first composited sample: nothing before it
+        // contributes (T = 1 and tau = 0 there), so its weights are the first pass's
         MarchState st2;
-        march<false, true>(s, r, st2, nullptr, 0, gf, grad_atlas);
+        march<false, true>(s, r, st2, nullptr, 0, gf, grad_atlas, k_first);
     }
 }
 

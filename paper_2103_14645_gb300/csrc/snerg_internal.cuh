@@ -264,10 +264,14 @@ __device__ __forceinline__ void accumulate_colour(MarchState& st, const uint2 cv
 // the march. TRACE records visited voxels; GRAD scatters w_k * trilinear weight * g
 // into the gradient atlas (density frozen, so the weights are the forward ones).
 // ---------------------------------------------------------------------------------
+// k_begin: first lattice index to consider (0, or a k known to precede every composited
+// sample, in which case the result is the same); k_first (nullable) receives the index
+// of the first composited sample (kmax if none).
 template <bool TRACE, bool GRAD>
 __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchState& st,
                                       uint64_t* trace, int trace_cap,
-                                      const float* gfeat, float* grad_atlas) {
+                                      const float* gfeat, float* grad_atlas,
+                                      int k_begin = 0, int* k_first = nullptr) {
 #pragma unroll
     for (int c = 0; c < 7; ++c) st.acc[c] = 0.0f;
     st.T = 1.0f;
@@ -281,8 +285,9 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
     float inv_d[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) inv_d[i] = __fdividef(1.0f, r.d[i]);
-    int k = 0;
+    int k = k_begin;
     bool done = false;
+    if (k_first) *k_first = s.kmax;
     for (;;) {
         if (k >= s.kmax) { st.limit = true; break; }
         const float t = lattice_t(r, k);
@@ -331,6 +336,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             if (TRACE && st.active < trace_cap)
                 trace[st.active] = ((uint64_t)(int)(lz + oz) * N + (uint64_t)(int)(ly + oy)) * N +
                                    (uint64_t)(int)(lx + ox);
+            if (k_first && st.active == 0) *k_first = kk;
             st.active++;
             // trilinear stencil on the virtual grid, cell-centred
             float f[3], g[3], fl[3];
