@@ -363,8 +363,9 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
         rb.render_rays(wsc.cameras, pix, wm, out=c)
 
     def fwd_bwd():
-        rb.render_rays(wsc.cameras, pix, wm, out=c)
-        rb.backward(wsc.cameras, pix, wm, c - tgt, ga, gm)
+        # a training step: the forward keeps its per-ray state for the backward's single march
+        f = rb.render_rays(wsc.cameras, pix, wm, out=c, aux=True, counts=True)
+        rb.backward(wsc.cameras, pix, wm, c - tgt, ga, gm, fwd_aux=f["aux"], fwd_counts=f["counts"])
 
     ms_f = time_steps(fwd, reps, 2, stream, flush)
     ms_fb = time_steps(fwd_bwd, reps, 2, stream, flush)
@@ -408,8 +409,8 @@ def large_section(args, dev, stream, flush):
         r.render_rays(sc.cameras, pix, mlp, out=c)
 
     def fwd_bwd():
-        r.render_rays(sc.cameras, pix, mlp, out=c)
-        r.backward(sc.cameras, pix, mlp, c - tgt, ga, gm)
+        f = r.render_rays(sc.cameras, pix, mlp, out=c, aux=True, counts=True)
+        r.backward(sc.cameras, pix, mlp, c - tgt, ga, gm, fwd_aux=f["aux"], fwd_counts=f["counts"])
 
     ms_f = time_steps(fwd, reps, 2, stream, flush)
     ms_fb = time_steps(fwd_bwd, reps, 2, stream, flush)

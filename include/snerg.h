@@ -80,7 +80,8 @@ typedef struct {
 typedef struct {
     float* d_aux;          /* [pixels][8]: C_d (3), V (4), accumulated opacity 1 - T */
     int32_t* d_counts;     /* [pixels][4]: steps (lattice samples in occupied blocks), active
-                              (composited) samples, indirection entries read, 0 */
+                              (composited) samples, indirection entries read, lattice index
+                              of the first composited sample (-1 if none) */
     uint64_t* d_trace;     /* [pixels][trace_cap]: z*N*N + y*N + x of each composited sample */
     int32_t trace_cap;
     int32_t persistent;    /* snerg_render only: 1 = all cameras in one persistent launch,
@@ -144,15 +145,21 @@ snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* cams, int32_t
                                float* d_rgb, const snerg_render_opts* opts, void* stream);
 
 /* Adjoint of snerg_render_rays for an upstream gradient d_grad_rgb [n][3] = dL/dC
- * (Sec. 5.5 fine-tunes against an L2 image loss, Eq. 3). Density is frozen. Each ray's
- * march is recomputed instead of stored. ACCUMULATES (caller zeroes):
+ * (Sec. 5.5 fine-tunes against an L2 image loss, Eq. 3). Density is frozen. Nothing
+ * per sample is stored: each ray is marched again. ACCUMULATES (caller zeroes):
  *   d_grad_atlas : float32 [num_blocks][B][B][B][8], dL/d(q/255) of channels 1..7 of
  *                  every stored voxel; channel 0 (density) receives exactly zero;
  *   d_grad_mlp   : float32 [SNERG_MLP_PARAMS].
- * Either gradient pointer may be NULL to skip it. */
+ * Either gradient pointer may be NULL to skip it. d_mlp must be device weights.
+ * d_fwd_aux / d_fwd_counts (both or neither, nullable): the opts.d_aux and
+ * opts.d_counts outputs of the snerg_render_rays call that produced C for these rays with
+ * the same cameras, rays and weights. Given them, the kernel takes C_d, V and the first
+ * composited lattice index from them (per-ray state, 9 words) instead of marching the
+ * ray twice; the gradients are the same. */
 snerg_status snerg_render_backward(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
                                    const int32_t* d_pix, int64_t n, const float* d_mlp,
-                                   const float* d_grad_rgb, float* d_grad_atlas,
+                                   const float* d_grad_rgb, const float* d_fwd_aux,
+                                   const int32_t* d_fwd_counts, float* d_grad_atlas,
                                    float* d_grad_mlp, void* stream);
 
 /* Ray-list render for callers that cannot allocate device memory. The paper has no

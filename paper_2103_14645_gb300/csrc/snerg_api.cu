@@ -420,7 +420,8 @@ extern "C" snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* ca
 
 extern "C" snerg_status snerg_render_backward(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
                                               const int32_t* d_pix, int64_t n, const float* d_mlp,
-                                              const float* d_grad_rgb, float* d_grad_atlas, float* d_grad_mlp,
+                                              const float* d_grad_rgb, const float* d_fwd_aux,
+                                              const int32_t* d_fwd_counts, float* d_grad_atlas, float* d_grad_mlp,
                                               void* stream) {
     if (!h || n < 0) return SNERG_E_INVAL;
     CamTable* t = new (std::nothrow) CamTable;
@@ -429,8 +430,9 @@ extern "C" snerg_status snerg_render_backward(snerg_handle h, const snerg_camera
     if (n == 0 || (!d_grad_atlas && !d_grad_mlp)) { delete t; return SNERG_OK; }
     if (!d_pix || !d_mlp || !d_grad_rgb) { delete t; return SNERG_E_INVAL; }
     if (d_grad_atlas && ((uintptr_t)d_grad_atlas & 15u)) { delete t; return SNERG_E_INVAL; }
-    cudaError_t e = launch_backward_rays(h->ds, *t, n_cams, d_pix, n, d_mlp, d_grad_rgb, d_grad_atlas, d_grad_mlp,
-                                         (cudaStream_t)stream);
+    if ((d_fwd_aux == nullptr) != (d_fwd_counts == nullptr)) { delete t; return SNERG_E_INVAL; }
+    cudaError_t e = launch_backward_rays(h->ds, *t, n_cams, d_pix, n, d_mlp, d_grad_rgb, d_fwd_aux, d_fwd_counts,
+                                         d_grad_atlas, d_grad_mlp, (cudaStream_t)stream);
     delete t;
     if (e != cudaSuccess) return SNERG_E_CUDA;
     h->launches++;

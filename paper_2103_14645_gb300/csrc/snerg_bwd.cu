@@ -98,9 +98,13 @@ __device__ __forceinline__ void mlp_forward_backward(const float* sW, float* row
     }
 }
 
+// fwd_aux / fwd_counts (nullable, both or neither): the forward's per-ray outputs
+// (C_d, V, opacity; steps, composited samples, indirection reads, first composited
+// lattice index). With them the kernel skips its own first march.
 __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     const DevScene s, const __grid_constant__ CamTable cams, int32_t n_cams, const int32_t* __restrict__ pix,
-    int64_t n, const float* __restrict__ mlp, const float* __restrict__ grad_rgb, float* __restrict__ grad_atlas,
+    int64_t n, const float* __restrict__ mlp, const float* __restrict__ grad_rgb,
+    const float* __restrict__ fwd_aux, const int32_t* __restrict__ fwd_counts, float* __restrict__ grad_atlas,
     float* __restrict__ grad_mlp) {
     extern __shared__ __align__(16) float smem[];
     float* sW = smem;
@@ -122,16 +126,34 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
             r = make_ray(s, cams.c[ci], px, py);
         else
             atomicCAS(s.status, 0, (int)SNERG_E_INVAL);
-        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr, 0, &k_first);
-        record_status(s, st);
+        if (fwd_aux) {
+            // the forward's per-ray state: C_d, V (decoded) and the first composited index
+            st.active = r.hit ? __ldg(fwd_counts + 4 * i + 1) : 0;
+            k_first = __ldg(fwd_counts + 4 * i + 3);
+#pragma unroll
+            for (int c = 0; c < 7; ++c) st.acc[c] = __ldg(fwd_aux + kAuxCh * i + c) * 255.0f;
+        } else {
+            march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr, 0, &k_first);
+            record_status(s, st);
+        }
     }
     const bool active = st.active > 0;
     float g[3] = {0.0f, 0.0f, 0.0f};
     float gx[7];
     if (active) {
         const float inv255 = 1.0f / 255.0f;
-        const float cd[3] = {st.acc[0] * inv255, st.acc[1] * inv255, st.acc[2] * inv255};
-        const float v[4] = {st.acc[3] * inv255, st.acc[4] * inv255, st.acc[5] * inv255, st.acc[6] * inv255};
+        float cd[3], v[4];
+        if (fwd_aux) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cd[c] = __ldg(fwd_aux + kAuxCh * i + c);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = __ldg(fwd_aux + kAuxCh * i + 3 + c);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cd[c] = st.acc[c] * inv255;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = st.acc[3 + c] * inv255;
+        }
         stage_mlp_input(row + kRowX, cd, v, r.d);
         g[0] = __ldg(grad_rgb + 3 * i);
         g[1] = __ldg(grad_rgb + 3 * i + 1);
@@ -177,8 +199,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
 }
 
 cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
-                                 int64_t n, const float* mlp, const float* grad_rgb, float* grad_atlas,
-                                 float* grad_mlp, cudaStream_t st) {
+                                 int64_t n, const float* mlp, const float* grad_rgb, const float* fwd_aux,
+                                 const int32_t* fwd_counts, float* grad_atlas, float* grad_mlp, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t smem = backward_smem_bytes();
     static bool attr_set = false;     // the opt-in for > 48 KB of dynamic shared memory
@@ -189,8 +211,8 @@ cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_
         attr_set = true;
     }
     const unsigned grid = (unsigned)((n + kBwdThreads - 1) / kBwdThreads);
-    backward_rays_kernel<<<grid, kBwdThreads, smem, st>>>(s, cams, n_cams, pix, n, mlp, grad_rgb, grad_atlas,
-                                                          grad_mlp);
+    backward_rays_kernel<<<grid, kBwdThreads, smem, st>>>(s, cams, n_cams, pix, n, mlp, grad_rgb, fwd_aux,
+                                                          fwd_counts, grad_atlas, grad_mlp);
     return cudaGetLastError();
 }
 

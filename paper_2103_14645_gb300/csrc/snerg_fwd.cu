@@ -39,10 +39,12 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const De
     const Ray r = make_ray(s, cam, px, py);
     const int64_t pix = cam.out_offset + (int64_t)py * cam.W + px;
     MarchState st;
+    int k_first = 0;
     if (DBG && dbg.trace)
-        march<true, false>(s, r, st, dbg.trace + pix * dbg.trace_cap, dbg.trace_cap, nullptr, nullptr);
+        march<true, false>(s, r, st, dbg.trace + pix * dbg.trace_cap, dbg.trace_cap, nullptr, nullptr, 0,
+                           &k_first);
     else
-        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
+        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr, 0, DBG ? &k_first : nullptr);
     record_status(s, st);
     float c[3], aux[kAuxCh];
     finish_ray(s, sW, nullptr, r, st, c, aux, PW ? &pw : nullptr);
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const De
             dbg.counts[pix * 4] = st.steps;
             dbg.counts[pix * 4 + 1] = st.active;
             dbg.counts[pix * 4 + 2] = st.blocks;
-            dbg.counts[pix * 4 + 3] = 0;
+            dbg.counts[pix * 4 + 3] = st.active > 0 ? k_first : -1;
         }
     }
 }
@@ -84,10 +86,11 @@ __global__ void __launch_bounds__(128, 8) render_rays_kernel(const DevScene s, c
         atomicCAS(s.status, 0, (int)SNERG_E_INVAL);
     }
     MarchState st;
+    int k_first = 0;
     if (DBG && dbg.trace)
-        march<true, false>(s, r, st, dbg.trace + i * dbg.trace_cap, dbg.trace_cap, nullptr, nullptr);
+        march<true, false>(s, r, st, dbg.trace + i * dbg.trace_cap, dbg.trace_cap, nullptr, nullptr, 0, &k_first);
     else
-        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
+        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr, 0, DBG ? &k_first : nullptr);
     record_status(s, st);
     float c[3], aux[kAuxCh];
     finish_ray(s, sW, nullptr, r, st, c, aux, PW ? &pw : nullptr);
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(128, 8) render_rays_kernel(const DevScene s, c
             dbg.counts[i * 4] = st.steps;
             dbg.counts[i * 4 + 1] = st.active;
             dbg.counts[i * 4 + 2] = st.blocks;
-            dbg.counts[i * 4 + 3] = 0;
+            dbg.counts[i * 4 + 3] = st.active > 0 ? k_first : -1;
         }
     }
 }

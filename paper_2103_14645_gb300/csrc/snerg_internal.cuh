@@ -715,8 +715,8 @@ cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t 
                                int64_t n, const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg,
                                cudaStream_t st);
 cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
-                                 const float* mlp, const float* grad_rgb, float* grad_atlas, float* grad_mlp,
-                                 cudaStream_t st);
+                                 const float* mlp, const float* grad_rgb, const float* fwd_aux,
+                                 const int32_t* fwd_counts, float* grad_atlas, float* grad_mlp, cudaStream_t st);
 cudaError_t launch_validate(const int32_t* ind, int64_t n_ind, int64_t nb, int32_t* blk_of_slot, int32_t* err,
                             cudaStream_t st);
 cudaError_t launch_build_padded(const int32_t* ind, const int32_t* blk_of_slot, const uint8_t* atlas, int64_t nb,

@@ -68,7 +68,7 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_render.restype = ctypes.c_int
     lib.snerg_render_rays.argtypes = [P, P, i32, P, i64, P, P, P, P]
     lib.snerg_render_rays.restype = ctypes.c_int
-    lib.snerg_render_backward.argtypes = [P, P, i32, P, i64, P, P, P, P, P]
+    lib.snerg_render_backward.argtypes = [P, P, i32, P, i64, P, P, P, P, P, P, P]
     lib.snerg_render_backward.restype = ctypes.c_int
     lib.snerg_last_status.argtypes = [P, P]
     lib.snerg_last_status.restype = ctypes.c_int
@@ -241,8 +241,11 @@ class Renderer:
         return out
 
     def backward(self, cams, pix: torch.Tensor, mlp: torch.Tensor, grad_rgb: torch.Tensor,
-                 grad_atlas: torch.Tensor | None = None, grad_mlp: torch.Tensor | None = None):
-        """Accumulate dL/d(atlas values) [nb,B,B,B,8] and dL/d(mlp) [883] for dL/dC."""
+                 grad_atlas: torch.Tensor | None = None, grad_mlp: torch.Tensor | None = None,
+                 fwd_aux: torch.Tensor | None = None, fwd_counts: torch.Tensor | None = None):
+        """Accumulate dL/d(atlas values) [nb,B,B,B,8] and dL/d(mlp) [883] for dL/dC.
+        fwd_aux / fwd_counts: the aux and counts outputs of the render_rays call that
+        produced C (then the rays are marched once instead of twice)."""
         c = _cams(cams)
         _require_cuda(pix, "pix", torch.int32)
         _require_cuda(mlp, "mlp", torch.float32)
@@ -253,9 +256,14 @@ class Renderer:
                 raise ValueError("grad_atlas must have nb*B^3*8 elements")
         if grad_mlp is not None:
             _require_cuda(grad_mlp, "grad_mlp", torch.float32)
+        if (fwd_aux is None) != (fwd_counts is None):
+            raise ValueError("fwd_aux and fwd_counts go together")
+        if fwd_aux is not None:
+            _require_cuda(fwd_aux, "fwd_aux", torch.float32)
+            _require_cuda(fwd_counts, "fwd_counts", torch.int32)
         code = self.lib.snerg_render_backward(self.handle, c.ctypes.data, c.shape[0], _ptr(pix), int(pix.shape[0]),
-                                              _ptr(mlp), _ptr(grad_rgb), _ptr(grad_atlas), _ptr(grad_mlp),
-                                              _stream(self.device))
+                                              _ptr(mlp), _ptr(grad_rgb), _ptr(fwd_aux), _ptr(fwd_counts),
+                                              _ptr(grad_atlas), _ptr(grad_mlp), _stream(self.device))
         _check(code, "snerg_render_backward")
 
 
@@ -271,20 +279,22 @@ class SnergRenderFn(torch.autograd.Function):
     def forward(ctx, mlp, atlas_values, renderer, cams, pix):
         ctx.renderer = renderer
         ctx.cams = cams
-        ctx.save_for_backward(mlp, pix)
         ctx.atlas_shape = atlas_values.shape
-        ctx.want_atlas = atlas_values.requires_grad
-        return renderer.render_rays(cams, pix, mlp.detach().contiguous())
+        out = renderer.render_rays(cams, pix, mlp.detach().contiguous(), aux=True, counts=True)
+        # per-ray state (C_d, V, first composited index) for the backward's single march
+        ctx.save_for_backward(mlp, pix, out["aux"], out["counts"])
+        return out["rgb"]
 
     @staticmethod
     def backward(ctx, grad_rgb):
-        mlp, pix = ctx.saved_tensors
+        mlp, pix, aux, counts = ctx.saved_tensors
         r = ctx.renderer
         g_mlp = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=r.device) if ctx.needs_input_grad[0] else None
         g_atl = (torch.zeros(ctx.atlas_shape, dtype=torch.float32, device=r.device)
                  if ctx.needs_input_grad[1] else None)
         if g_mlp is not None or g_atl is not None:
-            r.backward(ctx.cams, pix, mlp.detach().contiguous(), grad_rgb.contiguous().float(), g_atl, g_mlp)
+            r.backward(ctx.cams, pix, mlp.detach().contiguous(), grad_rgb.contiguous().float(), g_atl, g_mlp,
+                       fwd_aux=aux, fwd_counts=counts)
         return g_mlp, g_atl, None, None, None
 
 

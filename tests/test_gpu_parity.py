@@ -479,3 +479,29 @@ def test_step_limit_is_reported_and_cleared():
     full = renderer.Renderer.from_scene(sc, DEV)
     full.render(sc.cameras, w)
     full.check_status()
+
+
+def test_backward_with_forward_state_matches_recompute():
+    """Given the forward's per-ray outputs (C_d, V, first composited index) the backward
+    marches each ray once; its gradients equal those of the fully recomputing backward."""
+    sc = scene("bwd512")
+    pix_np, g_np = _bwd_case(sc, 16384, 41)
+    r = renderer.Renderer.from_scene(sc, DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    pix = torch.from_numpy(pix_np).to(DEV)
+    g = torch.from_numpy(g_np).to(DEV)
+    fwd = r.render_rays(sc.cameras, pix, w, aux=True, counts=True)
+    outs = []
+    for state in (False, True):
+        ga = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=DEV)
+        gm = torch.zeros(883, dtype=torch.float32, device=DEV)
+        kw = {"fwd_aux": fwd["aux"], "fwd_counts": fwd["counts"]} if state else {}
+        r.backward(sc.cameras, pix, w, g, ga, gm, **kw)
+        r.check_status()
+        outs.append((ga.cpu().numpy(), gm.cpu().numpy()))
+    (a0, m0), (a1, m1) = outs
+    assert np.abs(a0).max() > 0
+    np.testing.assert_allclose(a1, a0, rtol=0, atol=1e-6 * np.abs(a0).max())
+    np.testing.assert_allclose(m1, m0, rtol=0, atol=1e-6 * np.abs(m0).max())
+    c = fwd["counts"].cpu().numpy()
+    assert ((c[:, 3] >= 0) == (c[:, 1] > 0)).all()
