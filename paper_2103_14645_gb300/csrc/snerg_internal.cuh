@@ -285,6 +285,15 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
     float inv_d[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) inv_d[i] = __fdividef(1.0f, r.d[i]);
+    // Voxel-skip rate: between samples k and k+s every coordinate moves by at most
+    // s*m + eps voxels, m = max_i |d_i| and eps bounding the rounding of the binary32
+    // lattice arithmetic (a few ulps of the largest t or u the ray meets; max(t1, N) *
+    // 2^-19 is well above that). The nearest voxel then moves by at most s*m + eps + 1,
+    // so a sample whose nearest voxel is at Chebyshev distance D from every voxel with
+    // density is followed by empty samples for every s with s*m + eps < D - 1.
+    const float m_max = fmaxf(fmaxf(fabsf(r.d[0]), fabsf(r.d[1])), fabsf(r.d[2]));
+    const float skip_inv_m = (1.0f - 1.0f / 1048576.0f) / m_max;   // biased down: never overshoots
+    const float skip_eps = fmaxf(r.t1, s.fN) * (1.0f / 524288.0f);
     int k = k_begin;
     bool done = false;
     if (k_first) *k_first = s.kmax;
@@ -328,9 +337,10 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             const float lz = fminf(fmaxf(floorf(u[2]) - oz, 1.0f), Bf);
             const int vd = __ldg(vs + (int)fmaf(fmaf(lz, Pf, ly), Pf, lx));
             if (vd != 0) {
-                // no voxel of this block within Chebyshev distance vd-1 has density; the
-                // next vd-2 samples move at most vd-1 voxels per axis, so skip them
-                kk += max(1, vd - 1);
+                // no voxel of this block within Chebyshev distance vd-1 has density: the
+                // next s_max samples (s_max*m + eps < vd - 1) are empty, skip them
+                const float q = ((float)vd - 1.0f - skip_eps) * skip_inv_m;
+                kk += max(1, (int)ceilf(q));      // = 1 + s_max, s_max = ceil(q) - 1 >= 0
                 continue;
             }
             if (TRACE && st.active < trace_cap)
