@@ -166,10 +166,11 @@ extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t
     if (e == cudaSuccess) e = launch_voxel_distance(d_atlas, num_blocks, B, vtmp0, vtmp1, vskip, st);
     if (e == cudaSuccess)
         e = launch_build_padded(ws_ind, blk, d_atlas, num_blocks, N, B, ilog2_exact(B), patlas, st);
+    if (e == cudaSuccess) e = launch_fill_vskip_border(vskip, blk, num_blocks, N, B, ilog2_exact(B), st);
     if (e == cudaSuccess) e = launch_encode_distance(ws_ind, bdist, G3, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { delete h; return SNERG_E_CUDA; }
-    h->launches = 2 + 5 + (num_blocks > 0 ? 5 : 0);
+    h->launches = 2 + 5 + (num_blocks > 0 ? 6 : 0);
 
     DevScene& s = h->ds;
     s.ind = ws_ind;

@@ -321,21 +321,21 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
         // block origin minus one, so that the padded local coordinate is floor(u) - o
         const float ox = (float)((b[0] << s.lgB) - 1), oy = (float)((b[1] << s.lgB) - 1),
                     oz = (float)((b[2] << s.lgB) - 1);
-        const float Bf = (float)B, Pf = (float)P;
+        const float Pf = (float)P;
         int kk = k;
         while (kk < kx) {
             const float tk = lattice_t(r, kk);
             float u[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) u[i] = lattice_u(r, tk, i);
-            // nearest voxel in padded block coordinates: clamp(floor(u), 0, N-1) - origin + 1
-            // equals clamp(floor(u) - origin + 1, 1, B) for a sample of this block (the
-            // grid clamp only acts on the border blocks, where it coincides with the
-            // block clamp); all values are small integers, exact in binary32
-            const float lx = fminf(fmaxf(floorf(u[0]) - ox, 1.0f), Bf);
-            const float ly = fminf(fmaxf(floorf(u[1]) - oy, 1.0f), Bf);
-            const float lz = fminf(fmaxf(floorf(u[2]) - oz, 1.0f), Bf);
-            const int vd = __ldg(vs + (int)fmaf(fmaf(lz, Pf, ly), Pf, lx));
+            // nearest voxel in padded block coordinates, floor(u) - origin + 1: in [1, B] for
+            // a sample of this block, or 0 / B+1 where rounding puts u a hair outside the
+            // grid -- apron cells that hold the clamped edge voxel's value (the grid clamp
+            // is built into the plane); small integers, exact in binary32. The index clamp
+            // only guards the address.
+            const float lx = floorf(u[0]) - ox, ly = floorf(u[1]) - oy, lz = floorf(u[2]) - oz;
+            const int pidx = min(max((int)fmaf(fmaf(lz, Pf, ly), Pf, lx), 0), s.P3 - 1);
+            const int vd = __ldg(vs + pidx);
             if (vd != 0) {
                 // no voxel of this block within Chebyshev distance vd-1 has density: the
                 // next s_max samples (s_max*m + eps < vd - 1) are empty, skip them
@@ -344,8 +344,8 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 continue;
             }
             if (TRACE && st.active < trace_cap)
-                trace[st.active] = ((uint64_t)(int)(lz + oz) * N + (uint64_t)(int)(ly + oy)) * N +
-                                   (uint64_t)(int)(lx + ox);
+                trace[st.active] = ((uint64_t)nearest_voxel(u[2], N) * N + (uint64_t)nearest_voxel(u[1], N)) * N +
+                                   (uint64_t)nearest_voxel(u[0], N);
             if (k_first && st.active == 0) *k_first = kk;
             st.active++;
             // trilinear stencil on the virtual grid, cell-centred
@@ -357,11 +357,13 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 f[i] = __fsub_rn(x, fl[i]);
                 g[i] = __fsub_rn(1.0f, f[i]);
             }
-            const float l0x = fminf(fmaxf(fl[0] - ox, 0.0f), Bf);
-            const float l0y = fminf(fmaxf(fl[1] - oy, 0.0f), Bf);
-            const float l0z = fminf(fmaxf(fl[2] - oz, 0.0f), Bf);
-            const uint2* p0 = pa + (int)fmaf(fmaf(l0z, Pf, l0y), Pf, l0x);
+            // lower stencil corner in padded coordinates, in [0, B] for a sample of this block
+            // (the apron holds the neighbours and the clamped border); the index clamp only
+            // guards the address
             const int PP = P * P;
+            const int i0 = min(max((int)fmaf(fmaf(fl[2] - oz, Pf, fl[1] - oy), Pf, fl[0] - ox), 0),
+                               s.P3 - 1 - (PP + P + 1));
+            const uint2* p0 = pa + i0;
             uint2 cv[8];   // index = z*4 + y*2 + x
             cv[0] = __ldg(p0);
             cv[1] = __ldg(p0 + 1);
@@ -736,6 +738,8 @@ cudaError_t launch_build_padded(const int32_t* ind, const int32_t* blk_of_slot, 
 cudaError_t launch_block_distance(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
                                   uint8_t* bdist, cudaStream_t st);
 cudaError_t launch_encode_distance(int32_t* ind, const uint8_t* bdist, int64_t n, cudaStream_t st);
+cudaError_t launch_fill_vskip_border(uint8_t* vskip, const int32_t* blk_of_slot, int64_t nb, int N, int B, int lgB,
+                                     cudaStream_t st);
 cudaError_t launch_voxel_distance(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
                                   uint8_t* vskip, cudaStream_t st);
 

@@ -127,6 +127,34 @@ __global__ void encode_distance_kernel(int32_t* __restrict__ ind, const uint8_t*
         if (ind[t] < 0) ind[t] = -(int32_t)max((int)bdist[t], 1);
 }
 
+// Apron cells of the voxel-distance plane that lie outside the grid get the value of the
+// voxel they clamp to (clamp-to-edge, as in the padded atlas). A sample that rounding puts
+// a hair outside the grid then finds its clamped nearest voxel's value without a clamp.
+__global__ void fill_vskip_border_kernel(uint8_t* __restrict__ vskip, const int32_t* __restrict__ blk_of_slot,
+                                         int64_t nb, int N, int B, int lgB) {
+    const int P = B + 2, P3 = P * P * P, G = N >> lgB;
+    const int64_t total = nb * (int64_t)P3;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = t / P3;
+        const int r = (int)(t - slot * P3);
+        const int p[3] = {r % P, (r / P) % P, r / (P * P)};
+        if (p[0] >= 1 && p[0] <= B && p[1] >= 1 && p[1] <= B && p[2] >= 1 && p[2] <= B) continue;   // interior
+        const int blk = blk_of_slot[slot];
+        if (blk < 0) continue;
+        const int b[3] = {blk % G, (blk / G) % G, blk / (G * G)};
+        int q[3];
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int g = b[i] * B + p[i] - 1;
+            if (p[i] >= 1 && p[i] <= B) { q[i] = p[i]; continue; }
+            if (g >= 0 && g < N) { ok = false; break; }      // faces an interior neighbour: never probed
+            q[i] = min(max(g, 0), N - 1) - b[i] * B + 1;     // the clamped voxel, inside this block
+        }
+        if (ok) vskip[t] = vskip[slot * P3 + (q[2] * P + q[1]) * P + q[0]];
+    }
+}
+
 static unsigned grid_for(int64_t n) {
     const int64_t b = (n + 255) / 256;
     return (unsigned)(b < 1048576 ? (b > 0 ? b : 1) : 1048576);
@@ -178,6 +206,16 @@ namespace snerg {
 cudaError_t launch_encode_distance(int32_t* ind, const uint8_t* bdist, int64_t n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     encode_distance_kernel<<<grid_for(n), 256, 0, st>>>(ind, bdist, n);
+    return cudaGetLastError();
+}
+}  // namespace snerg
+
+namespace snerg {
+cudaError_t launch_fill_vskip_border(uint8_t* vskip, const int32_t* blk_of_slot, int64_t nb, int N, int B, int lgB,
+                                     cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    fill_vskip_border_kernel<<<grid_for(nb * (int64_t)(B + 2) * (B + 2) * (B + 2)), 256, 0, st>>>(vskip, blk_of_slot,
+                                                                                              nb, N, B, lgB);
     return cudaGetLastError();
 }
 }  // namespace snerg
