@@ -48,7 +48,7 @@ def _lib():
             build_oracle()
         lib = ctypes.CDLL(_SO)
         P, i32, i64, f32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
-        common = [i32, i32, P, f32, f64, P, P, P, P, i64, P, P, i32, P, i64]
+        common = [i32, i32, P, f32, f64, P, P, P, P, i64, i32, P, P, i32, P, i64]
         lib.oracle_render_rays.argtypes = common + [P, P, P, P, i32]
         lib.oracle_render_rays.restype = ctypes.c_int
         lib.oracle_backward_rays.argtypes = common + [P, P, P]
@@ -93,15 +93,17 @@ def _scene_args(scene, val, mlp, cams):
     assert w.size == NPARAM
     cf = cameras_f32(scene.cameras if cams is None else cams)
     keep = (bmin, bg, ind, atlas, val, w, cf)
+    flags = int(getattr(scene, "flags", 0))
     args = [int(scene.N), int(scene.B), _p(bmin), float(np.float32(scene.extent)),
             float(np.float32(scene.sigma_max)), _p(bg),
-            _p(ind), _p(atlas), _p(val), int(atlas.shape[0]), _p(w), _p(cf), int(cf.shape[0])]
+            _p(ind), _p(atlas), _p(val), int(atlas.shape[0]), flags, _p(w), _p(cf), int(cf.shape[0])]
     return args, keep
 
 
 def render_rays(scene, pix, mlp=None, val=None, cams=None, trace_cap: int = 0):
     """Render rays pix[n][3] = (camera, x, y). Returns a dict with
-    rgb [n,3] f64, aux [n,8] f64 (C_d, V, acc), counts [n,2] int32 (steps, active) and,
+    rgb [n,3] f64, aux [n,8] f64 (C_d, V, acc before any un-premultiply), counts [n,2]
+    int32 (steps, active) and,
     when trace_cap > 0, trace [n,trace_cap] uint64 (visited voxel indices, 0-padded)."""
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 3)
     n = pix.shape[0]

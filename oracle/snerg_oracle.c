@@ -18,6 +18,9 @@
  *   * if any sample was composited, the tiny MLP (2 hidden layers of 16, Sec. 4.2)
  *     adds a view-dependent residual (Eq. 7): C = C_d + sigmoid(MLP(C_d, V, PE(d))),
  *     plus T_final * background (App. A evaluates the MLP only where alpha > 0);
+ *   * optional partial un-premultiply (App. C, forward-facing scenes): after compositing,
+ *     (C_d, alpha, V) *= min(1, 1.5 alpha) / alpha where alpha = 1 - T_final > 0, so the
+ *     MLP sees the scaled C_d and V and the background weight becomes 1 - min(1, 1.5 alpha);
  *   * the backward pass is the exact adjoint of the above w.r.t. the decoded colour and
  *     feature values and the MLP weights, with density frozen (Sec. 5.5 fine-tunes the
  *     per-pixel network against an L2 image loss, Eq. 3).
@@ -72,6 +75,7 @@ typedef struct {
     float taumax32;        /* binary32(ln 1000) */
     double delta;          /* voxel width in world units, extent / N */
     int64_t max_iter;
+    int unpremultiply;     /* App. C partial un-premultiply */
 } OScene;
 
 /* ------------------------------------------------------------------------- */
@@ -259,6 +263,19 @@ static void march(const OScene* S, const ORay* r, uint64_t* trace, int32_t trace
     }
 }
 
+/* App. C: (C_d, alpha, V) *= min(1, 1.5 alpha) / alpha when alpha = 1 - T > 0. Returns the
+ * scale (1 when not applied) and rewrites m->cd, m->v and m->T accordingly. */
+static double unpremultiply(const OScene* S, OMarch* m) {
+    double a = 1.0 - m->T;
+    if (!S->unpremultiply || !(a > 0.0)) return 1.0;
+    double a2 = 1.5 * a < 1.0 ? 1.5 * a : 1.0;
+    double sc = a2 / a;
+    for (int c = 0; c < 3; ++c) m->cd[c] *= sc;
+    for (int c = 0; c < 4; ++c) m->v[c] *= sc;
+    m->T = 1.0 - a2;
+    return sc;
+}
+
 /* ------------------------------------------------------------------------- */
 /* view-dependence MLP, Eq. 7: 34 -> 16 ReLU -> 16 ReLU -> 3 -> sigmoid       */
 
@@ -335,7 +352,8 @@ static void mlp_backward(const double* w, const double x[MLP_IN], const OMlp* m,
 /* exported entry points                                                      */
 
 static int scene_init(OScene* S, int32_t N, int32_t B, const float* bmin, float extent, double sigma_max,
-                      const double* bg, const int32_t* ind, const uint8_t* atlas, const double* val, int64_t nb) {
+                      const double* bg, const int32_t* ind, const uint8_t* atlas, const double* val, int64_t nb,
+                      int32_t flags) {
     if (N <= 0 || B <= 0 || N % B != 0 || !(extent > 0.0f)) return OR_E_INVAL;
     S->N = N; S->B = B; S->G = N / B;
     for (int i = 0; i < 3; ++i) { S->bmin[i] = bmin[i]; S->bg[i] = bg[i]; }
@@ -346,6 +364,7 @@ static int scene_init(OScene* S, int32_t N, int32_t B, const float* bmin, float 
     S->kappa32 = (float)(sigma_max * ((double)extent / (double)N) / 255.0);
     S->taumax32 = (float)log(1000.0);
     S->max_iter = 4 * (int64_t)N + 16;
+    S->unpremultiply = (flags & 1) != 0;
     for (int64_t i = 0; i < (int64_t)S->G * S->G * S->G; ++i)
         if (ind[i] < -1 || ind[i] >= nb) return OR_E_INVAL;
     return OR_OK;
@@ -356,11 +375,11 @@ static int scene_init(OScene* S, int32_t N, int32_t B, const float* bmin, float 
  *   trace[n][trace_cap] = linear indices z*N*N + y*N + x of composited samples.
  * Returns 0, or the first nonzero ray status. */
 int oracle_render_rays(int32_t N, int32_t B, const float* bmin, float extent, double sigma_max, const double* bg,
-                       const int32_t* ind, const uint8_t* atlas, const double* val, int64_t nb,
+                       const int32_t* ind, const uint8_t* atlas, const double* val, int64_t nb, int32_t flags,
                        const double* mlp, const float* cams, int32_t n_cams, const int32_t* pix, int64_t n,
                        double* rgb, double* aux, int32_t* counts, uint64_t* trace, int32_t trace_cap) {
     OScene S;
-    int st = scene_init(&S, N, B, bmin, extent, sigma_max, bg, ind, atlas, val, nb);
+    int st = scene_init(&S, N, B, bmin, extent, sigma_max, bg, ind, atlas, val, nb, flags);
     if (st) return st;
     int err = 0;
     #pragma omp parallel for schedule(dynamic, 64)
@@ -378,6 +397,11 @@ int oracle_render_rays(int32_t N, int32_t B, const float* bmin, float extent, do
             #pragma omp atomic write
             err = m.status;
         }
+        const double raw_T = m.T;
+        double raw_cd[3], raw_v[4];
+        for (int c = 0; c < 3; ++c) raw_cd[c] = m.cd[c];
+        for (int c = 0; c < 4; ++c) raw_v[c] = m.v[c];
+        unpremultiply(&S, &m);
         double res[3] = {0.0, 0.0, 0.0};
         if (m.active > 0) {
             double x[MLP_IN];
@@ -387,10 +411,10 @@ int oracle_render_rays(int32_t N, int32_t B, const float* bmin, float extent, do
             for (int c = 0; c < 3; ++c) res[c] = mm.res[c];
         }
         for (int c = 0; c < 3; ++c) rgb[3 * i + c] = (m.active > 0 ? m.cd[c] + res[c] : 0.0) + m.T * S.bg[c];
-        if (aux) {
-            for (int c = 0; c < 3; ++c) aux[8 * i + c] = m.cd[c];
-            for (int c = 0; c < 4; ++c) aux[8 * i + 3 + c] = m.v[c];
-            aux[8 * i + 7] = 1.0 - m.T;
+        if (aux) {       /* the composites before any un-premultiply */
+            for (int c = 0; c < 3; ++c) aux[8 * i + c] = raw_cd[c];
+            for (int c = 0; c < 4; ++c) aux[8 * i + 3 + c] = raw_v[c];
+            aux[8 * i + 7] = 1.0 - raw_T;
         }
         if (counts) { counts[2 * i] = m.steps; counts[2 * i + 1] = m.active; }
     }
@@ -402,11 +426,11 @@ int oracle_render_rays(int32_t N, int32_t B, const float* bmin, float extent, do
  * density, is frozen and left untouched; grad may be NULL to skip it) and dL/d(MLP
  * weights) into gmlp[883]. */
 int oracle_backward_rays(int32_t N, int32_t B, const float* bmin, float extent, double sigma_max, const double* bg,
-                         const int32_t* ind, const uint8_t* atlas, const double* val, int64_t nb,
+                         const int32_t* ind, const uint8_t* atlas, const double* val, int64_t nb, int32_t flags,
                          const double* mlp, const float* cams, int32_t n_cams, const int32_t* pix, int64_t n,
                          const double* g_rgb, double* grad, double* gmlp) {
     OScene S;
-    int st = scene_init(&S, N, B, bmin, extent, sigma_max, bg, ind, atlas, val, nb);
+    int st = scene_init(&S, N, B, bmin, extent, sigma_max, bg, ind, atlas, val, nb, flags);
     if (st) return st;
     int err = 0;
     #pragma omp parallel
@@ -428,6 +452,8 @@ int oracle_backward_rays(int32_t N, int32_t B, const float* bmin, float extent, 
                 err = m.status;
             }
             if (m.active == 0) continue;          /* C = T bg: no parameter reaches the output */
+            /* the un-premultiply scale depends on density only (frozen): a constant factor */
+            const double sc = unpremultiply(&S, &m);
             double x[MLP_IN], gx[MLP_IN];
             OMlp mm;
             mlp_input(m.cd, m.v, r.d, x);
@@ -436,8 +462,8 @@ int oracle_backward_rays(int32_t N, int32_t B, const float* bmin, float extent, 
             mlp_backward(mlp, x, &mm, g, gl, gx);
             if (!grad) continue;                  /* only dL/dPhi requested */
             double gf[7];
-            for (int c = 0; c < 3; ++c) gf[c] = g[c] + gx[c];      /* C = C_d + residual */
-            for (int c = 0; c < 4; ++c) gf[3 + c] = gx[3 + c];
+            for (int c = 0; c < 3; ++c) gf[c] = sc * (g[c] + gx[c]);      /* C = s C_d + residual */
+            for (int c = 0; c < 4; ++c) gf[3 + c] = sc * gx[3 + c];
             OMarch m2;
             march(&S, &r, NULL, 0, gf, grad, &m2);
         }

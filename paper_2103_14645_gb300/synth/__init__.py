@@ -97,6 +97,7 @@ class Scene:
     mlp: np.ndarray            # float32 [883]
     cameras: np.ndarray        # CAMERA_DTYPE [n_cams]
     extra: dict = field(default_factory=dict)
+    flags: int = 0             # bit 0: partial un-premultiply after compositing (App. C)
 
     @property
     def G(self) -> int:
@@ -371,9 +372,9 @@ def all_pixels(cams: np.ndarray) -> np.ndarray:
 
 def custom_scene(N: int, B: int, ind: np.ndarray, atlas: np.ndarray, sigma_max: float,
                  mlp: np.ndarray, cameras: np.ndarray, bmin=WORLD_BMIN, extent=WORLD_EXTENT,
-                 bg=BG, name="custom") -> Scene:
+                 bg=BG, name="custom", flags: int = 0) -> Scene:
     """Wrap hand-built arrays (tests) in a Scene."""
     return Scene(name=name, N=N, B=B, bmin=tuple(bmin), extent=float(extent),
                  sigma_max=float(sigma_max), bg=tuple(bg), ind=np.ascontiguousarray(ind, np.int32),
                  atlas=np.ascontiguousarray(atlas, np.uint8), mlp=np.ascontiguousarray(mlp, np.float32),
-                 cameras=np.ascontiguousarray(cameras))
+                 cameras=np.ascontiguousarray(cameras), flags=int(flags))

@@ -202,7 +202,7 @@ def test_mlp_input_layout():
     np.testing.assert_allclose(x, np.concatenate(ref), rtol=0, atol=1e-15)
 
 
-def _brute_force_ray(scene, dense, mlp, cam, px, py):
+def _brute_force_ray(scene, dense, mlp, cam, px, py, unpremultiply=False):
     """Definition of the march evaluated by library routines on a dense grid:
     trilinear by scipy.ndimage.map_coordinates (order 1, clamp-to-edge), transmittance
     by a running product, MLP by torch float64 linear layers."""
@@ -239,6 +239,12 @@ def _brute_force_ray(scene, dense, mlp, cam, px, py):
         tau += sd
         if tau > math.log(1000.0):
             break
+    raw = feat.copy()
+    if unpremultiply and 1 - T > 0:
+        a = 1 - T
+        sc = min(1.0, 1.5 * a) / a
+        feat = feat * sc
+        T = 1 - min(1.0, 1.5 * a)
     rgb = np.asarray(scene.bg) * T
     if visited:
         dd = np.asarray(d, np.float64)
@@ -246,12 +252,13 @@ def _brute_force_ray(scene, dense, mlp, cam, px, py):
         for l in range(4):
             pe += [np.sin(2.0 ** l * dd), np.cos(2.0 ** l * dd)]
         rgb = rgb + feat[:3] + _torch_mlp(mlp, np.concatenate(pe)[None])[0]
-    return rgb, feat, steps, visited
+    return rgb, raw, steps, visited
 
 
-@pytest.mark.parametrize("name", ["tiny", "gauss64"])
-def test_brute_force_dense_grid(name):
+@pytest.mark.parametrize("name,unpremultiply", [("tiny", False), ("gauss64", False), ("gauss64", True)])
+def test_brute_force_dense_grid(name, unpremultiply):
     sc = synth.make_scene(name)
+    sc.flags = 1 if unpremultiply else 0
     dense = helpers.blocks_to_dense(sc)
     rng = np.random.default_rng(5)
     W, H = int(sc.cameras[0]["W"]), int(sc.cameras[0]["H"])
@@ -259,7 +266,7 @@ def test_brute_force_dense_grid(name):
     out = oracle.render_rays(sc, pix, trace_cap=256)
     n_active_rays = 0
     for i, (c, x, y) in enumerate(pix):
-        rgb, feat, steps, visited = _brute_force_ray(sc, dense, sc.mlp, sc.cameras[c], x, y)
+        rgb, feat, steps, visited = _brute_force_ray(sc, dense, sc.mlp, sc.cameras[c], x, y, unpremultiply)
         np.testing.assert_allclose(out["rgb"][i], rgb, rtol=0, atol=1e-10)
         np.testing.assert_allclose(out["aux"][i, :7], feat, rtol=0, atol=1e-10)
         assert out["counts"][i, 0] == steps
@@ -386,3 +393,62 @@ def test_paper_constants():
     assert 8 * 8 == g["bytes_per_trilinear_sample"]["value"]
     assert synth.make_scene("shell1024").B == g["macroblock_edge"]["value"]
     assert synth.MLP_IN - 7 == 3 + 3 * 2 * 4    # direction + 4 octaves of sin/cos
+
+
+
+# --------------------------------------------------------------------------------------
+# partial un-premultiply (App. C): (C_d, alpha, V) *= min(1, 1.5 alpha) / alpha
+# --------------------------------------------------------------------------------------
+
+def test_unpremultiply_slab_closed_form():
+    col = np.array([100, 150, 200, 10, 20, 30, 40])
+    sc = helpers.slab_scene(z_range=(4, 6), q=60, color=col, sigma_max_vox=1.0)
+    sc.flags = 1
+    out = oracle.render_rays(sc, np.array([[0, 0, 0]]))
+    T = math.exp(-2 * 60 / 255.0)
+    a = 1 - T
+    a2 = min(1.0, 1.5 * a)
+    assert a2 < 1.0                                   # the soft-edge branch
+    cd = col[:3] / 255.0 * a * (a2 / a)
+    np.testing.assert_allclose(out["rgb"][0], cd + (1 - a2) * np.asarray(sc.bg), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(out["aux"][0, 7], a, rtol=0, atol=1e-14)     # aux keeps the raw opacity
+
+
+def test_unpremultiply_saturates_to_the_surface_colour():
+    """Opacity above 2/3 is fully saturated: a uniform slab then shows exactly its own
+    colour and no background."""
+    col = np.array([100, 150, 200, 10, 20, 30, 40])
+    sc = helpers.slab_scene(z_range=(4, 6), q=255, color=col, sigma_max_vox=1.0)
+    sc.flags = 1
+    out = oracle.render_rays(sc, np.array([[0, 0, 0]]))
+    assert 1 - math.exp(-2.0) > 2.0 / 3.0
+    np.testing.assert_allclose(out["rgb"][0], col[:3] / 255.0, rtol=0, atol=1e-14)
+
+
+def test_unpremultiply_gradient_matches_central_differences():
+    sc = synth.make_scene("tiny")
+    sc.flags = 1
+    rng = np.random.default_rng(22)
+    pix = _pix(sc)
+    target = rng.uniform(size=(pix.shape[0], 3))
+    val = sc.atlas.astype(np.float64) / 255.0
+    mlp = sc.mlp.astype(np.float64)
+    L0, out = _loss(sc, pix, target, val, mlp)
+    gval, gmlp = oracle.backward_rays(sc, pix, out["rgb"] - target, val=val, mlp=mlp)
+    h = 1e-6
+    flat = gval.reshape(-1)
+    nz = np.nonzero(np.abs(flat) > 1e-6)[0]
+    nz = nz[nz % 8 != 0]
+    for idx in rng.choice(nz, 16, replace=False):
+        vp, vm = val.copy().reshape(-1), val.copy().reshape(-1)
+        vp[idx] += h
+        vm[idx] -= h
+        fd = (_loss(sc, pix, target, vp.reshape(val.shape), mlp)[0] -
+              _loss(sc, pix, target, vm.reshape(val.shape), mlp)[0]) / (2 * h)
+        assert abs(fd - flat[idx]) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, flat[idx])
+    for p in rng.choice(synth.MLP_NPARAM, 16, replace=False):
+        mp, mm = mlp.copy(), mlp.copy()
+        mp[p] += h
+        mm[p] -= h
+        fd = (_loss(sc, pix, target, val, mp)[0] - _loss(sc, pix, target, val, mm)[0]) / (2 * h)
+        assert abs(fd - gmlp[p]) <= 1e-6 * max(1.0, abs(fd)), (p, fd, gmlp[p])
