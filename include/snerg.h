@@ -63,7 +63,14 @@ typedef struct {
     int32_t max_steps;  /* cap on the lattice index of a ray; 0 = 4N + 16 (never reached by a
                            valid ray). A ray reaching the cap stops, keeps what it composited
                            and records SNERG_E_STEP_LIMIT in the device status word. */
+    int32_t flags;      /* SNERG_FLAG_* */
 } snerg_scene_desc;
+
+/* Partial un-premultiply after compositing (the paper's forward-facing scenes, App. C):
+ * when alpha = 1 - T_final > 0, (C_d, alpha, V) *= min(1, 1.5 alpha) / alpha, so the MLP
+ * sees the scaled C_d and V and the background weight is 1 - min(1, 1.5 alpha). The aux
+ * output keeps the composites before scaling. */
+#define SNERG_FLAG_UNPREMULTIPLY 1
 
 /* Pinhole camera (Sec. 4.1 r(t) = o + t d). 80 bytes, host memory.
  * Pixel (x, y) looks along R (x + 0.5 - cx) / fx, -(y + 0.5 - cy) / fy, -1) normalised,

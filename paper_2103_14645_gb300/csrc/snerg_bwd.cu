@@ -140,20 +140,30 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     const bool active = st.active > 0;
     float g[3] = {0.0f, 0.0f, 0.0f};
     float gx[7];
+    float sc = 1.0f;
     if (active) {
         const float inv255 = 1.0f / 255.0f;
         float cd[3], v[4];
+        float T;
         if (fwd_aux) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) cd[c] = __ldg(fwd_aux + kAuxCh * i + c);
 #pragma unroll
             for (int c = 0; c < 4; ++c) v[c] = __ldg(fwd_aux + kAuxCh * i + 3 + c);
+            T = 1.0f - __ldg(fwd_aux + kAuxCh * i + 7);
         } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) cd[c] = st.acc[c] * inv255;
 #pragma unroll
             for (int c = 0; c < 4; ++c) v[c] = st.acc[3 + c] * inv255;
+            T = st.T;
         }
+        // App. C un-premultiply: a density-only (frozen) scale on C_d and V
+        sc = unpremultiply_scale(s, T);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cd[c] *= sc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] *= sc;
         stage_mlp_input(row + kRowX, cd, v, r.d);
         g[0] = __ldg(grad_rgb + 3 * i);
         g[1] = __ldg(grad_rgb + 3 * i + 1);
@@ -188,9 +198,9 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     if (active && grad_atlas) {
         float gf[7];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) gf[c] = g[c] + gx[c];     // C = C_d + residual
+        for (int c = 0; c < 3; ++c) gf[c] = sc * (g[c] + gx[c]);     // C = s C_d + residual
 #pragma unroll
-        for (int c = 0; c < 4; ++c) gf[3 + c] = gx[3 + c];
+        for (int c = 0; c < 4; ++c) gf[3 + c] = sc * gx[3 + c];
         // the second pass starts at the first composited sample: nothing before it
         // contributes (T = 1 and tau = 0 there), so its weights are the first pass's
         MarchState st2;

@@ -72,7 +72,16 @@ struct DevScene {
     float taumax;     // binary32(ln 1000)
     float bg[3];
     int32_t kmax;     // lattice index cap (4N + 16)
+    int32_t flags;    // SNERG_FLAG_*
 };
+
+// App. C: the scale min(1, 1.5 a) / a applied after compositing to (C_d, alpha, V) when
+// un-premultiply is on and a = 1 - T > 0 (else 1). Depends on density only.
+__device__ __forceinline__ float unpremultiply_scale(const DevScene& s, float T) {
+    const float a = 1.0f - T;
+    if (!(s.flags & SNERG_FLAG_UNPREMULTIPLY) || !(a > 0.0f)) return 1.0f;
+    return fminf(1.0f, 1.5f * a) / a;
+}
 
 struct CamTable {
     snerg_camera c[kMaxCams];
@@ -683,6 +692,20 @@ __device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, f
     for (int c = 0; c < 3; ++c) cd[c] = st.acc[c] * inv255;
 #pragma unroll
     for (int c = 0; c < 4; ++c) v[c] = st.acc[3 + c] * inv255;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) aux[c] = cd[c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) aux[3 + c] = v[c];
+    aux[7] = 1.0f - st.T;
+    float T = st.T;
+    if (s.flags & SNERG_FLAG_UNPREMULTIPLY) {
+        const float sc = unpremultiply_scale(s, st.T);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cd[c] *= sc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] *= sc;
+        T = 1.0f - (1.0f - st.T) * sc;
+    }
     float res[3] = {0.0f, 0.0f, 0.0f};
     if (st.active > 0) {
         float m[3];
@@ -698,12 +721,7 @@ __device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, f
         for (int c = 0; c < 3; ++c) res[c] = cd[c] + m[c];
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rgb[c] = res[c] + st.T * s.bg[c];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) aux[c] = cd[c];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) aux[3 + c] = v[c];
-    aux[7] = 1.0f - st.T;
+    for (int c = 0; c < 3; ++c) rgb[c] = res[c] + T * s.bg[c];
 }
 
 __device__ __forceinline__ void record_status(const DevScene& s, const MarchState& st) {

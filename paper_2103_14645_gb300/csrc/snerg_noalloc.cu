@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(128, 8) render_rays_noalloc_kernel(const DevSc
 
 bool desc_ok_noalloc(const snerg_scene_desc* d) {
     if (!d || d->N < 1 || d->N > 16384 || d->B < 2 || d->B > 64 || (d->B & (d->B - 1)) || d->N % d->B) return false;
-    if (d->max_steps < 0) return false;
+    if (d->max_steps < 0 || (d->flags & ~SNERG_FLAG_UNPREMULTIPLY)) return false;
     if (!(d->extent > 0.0f) || !(d->extent < INFINITY) || !(d->sigma_max >= 0.0f) || !(d->sigma_max < INFINITY))
         return false;
     for (int i = 0; i < 3; ++i)
@@ -275,6 +275,7 @@ extern "C" snerg_status snerg_render_rays_noalloc(const snerg_scene_desc* desc, 
         }
         s.kappa = (float)((double)desc->sigma_max * ((double)desc->extent / (double)N) / 255.0);
         s.taumax = (float)std::log(1000.0);
+        s.flags = desc->flags;
         s.kmax = desc->max_steps > 0 ? (desc->max_steps < 4 * N + 16 ? desc->max_steps : 4 * N + 16) : 4 * N + 16;
         render_rays_noalloc_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
             s, reinterpret_cast<const uint2*>(d_atlas), num_blocks, table, n_cams, d_pix, n, d_mlp, d_rgb);

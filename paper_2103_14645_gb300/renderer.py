@@ -17,6 +17,7 @@ from . import synth
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsnerg.so")
 MLP_PARAMS = 883
+FLAG_UNPREMULTIPLY = 1
 MAX_CAMERAS = 256
 AUX_CH = 8
 
@@ -38,7 +39,7 @@ class SnergError(RuntimeError):
 class SceneDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("B", ctypes.c_int32), ("bmin", ctypes.c_float * 3),
                 ("extent", ctypes.c_float), ("sigma_max", ctypes.c_float), ("bg", ctypes.c_float * 3),
-                ("max_steps", ctypes.c_int32)]
+                ("max_steps", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class RenderOpts(ctypes.Structure):
@@ -119,7 +120,7 @@ class Renderer:
     """A baked SNeRG scene resident on one GPU (snerg_create) and its render calls."""
 
     def __init__(self, N: int, B: int, bmin, extent: float, sigma_max: float, bg,
-                 indirection: torch.Tensor, atlas: torch.Tensor, max_steps: int = 0):
+                 indirection: torch.Tensor, atlas: torch.Tensor, max_steps: int = 0, flags: int = 0):
         self.lib = load_library()
         _require_cuda(indirection, "indirection", torch.int32)
         _require_cuda(atlas, "atlas", torch.uint8)
@@ -127,7 +128,7 @@ class Renderer:
         self.N, self.B = int(N), int(B)
         self.nb = int(atlas.shape[0]) if atlas.dim() > 0 else 0
         self.desc = SceneDesc(self.N, self.B, (ctypes.c_float * 3)(*bmin), float(extent),
-                              float(sigma_max), (ctypes.c_float * 3)(*bg), int(max_steps))
+                              float(sigma_max), (ctypes.c_float * 3)(*bg), int(max_steps), int(flags))
         nbytes = self.lib.snerg_workspace_bytes(ctypes.byref(self.desc), self.nb)
         if nbytes == 0:
             raise ValueError("invalid scene description")
@@ -143,7 +144,8 @@ class Renderer:
     def from_scene(cls, scene, device="cuda", max_steps: int = 0) -> "Renderer":
         ind = torch.from_numpy(np.ascontiguousarray(scene.ind, np.int32)).to(device)
         atl = torch.from_numpy(np.ascontiguousarray(scene.atlas, np.uint8)).to(device)
-        return cls(scene.N, scene.B, scene.bmin, scene.extent, scene.sigma_max, scene.bg, ind, atl, max_steps)
+        return cls(scene.N, scene.B, scene.bmin, scene.extent, scene.sigma_max, scene.bg, ind, atl, max_steps,
+                   int(getattr(scene, "flags", 0)))
 
     # ---------------------------------------------------------------------------------
     def close(self):

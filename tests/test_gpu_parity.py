@@ -505,3 +505,46 @@ def test_backward_with_forward_state_matches_recompute():
     np.testing.assert_allclose(m1, m0, rtol=0, atol=1e-6 * np.abs(m0).max())
     c = fwd["counts"].cpu().numpy()
     assert ((c[:, 3] >= 0) == (c[:, 1] > 0)).all()
+
+
+# --------------------------------------------------------------------------------------
+# partial un-premultiply (App. C)
+# --------------------------------------------------------------------------------------
+
+def _unpremultiplied(name):
+    sc0 = scene(name)
+    return synth.custom_scene(sc0.N, sc0.B, sc0.ind, sc0.atlas, sc0.sigma_max, sc0.mlp, sc0.cameras,
+                              flags=renderer.FLAG_UNPREMULTIPLY)
+
+
+def test_unpremultiply_forward_parity():
+    sc = _unpremultiplied("gauss64")
+    g, r = gpu_render(sc, aux=True, counts=True, trace_cap=64)
+    o = oracle_all(sc, trace_cap=64)
+    assert_parity(g, o)
+    plain = oracle_all(scene("gauss64"))
+    assert np.abs(o["rgb"] - plain["rgb"]).max() > 1e-2          # the option changes the image
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    r.set_mlp(sc.mlp)
+    for kw in ({}, {"persistent": True, "tile": (8, 4), "ctas_per_sm": 2}):
+        got = r.render(sc.cameras, None, **kw).cpu().numpy()
+        assert np.abs(got - o["rgb"]).max() <= TOL
+
+
+def test_unpremultiply_backward_parity():
+    sc = _unpremultiplied("gauss64")
+    pix, g = _bwd_case(sc, 4096, 51)
+    ga, gm, r = gpu_backward(sc, pix, g)
+    ra, rm = oracle.backward_rays(sc, pix, g)
+    assert np.abs(ga - ra).max() <= 1e-4 * np.abs(ra).max()
+    assert np.abs(gm - rm).max() <= 1e-4 * np.abs(rm).max()
+    # the same through the forward's per-ray state
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    pt = torch.from_numpy(pix).to(DEV)
+    fwd = r.render_rays(sc.cameras, pt, w, aux=True, counts=True)
+    ga2 = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=DEV)
+    gm2 = torch.zeros(883, dtype=torch.float32, device=DEV)
+    r.backward(sc.cameras, pt, w, torch.from_numpy(g).to(DEV), ga2, gm2, fwd_aux=fwd["aux"], fwd_counts=fwd["counts"])
+    r.check_status()
+    assert np.abs(ga2.cpu().numpy() - ra).max() <= 1e-4 * np.abs(ra).max()
+    assert np.abs(gm2.cpu().numpy() - rm).max() <= 1e-4 * np.abs(rm).max()

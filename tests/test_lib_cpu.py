@@ -50,7 +50,7 @@ def test_nm_shows_c_linkage(lib):
 
 
 def _desc(N=64, B=8, extent=2.0, sigma=10.0):
-    return renderer.SceneDesc(N, B, (ctypes.c_float * 3)(-1, -1, -1), extent, sigma, (ctypes.c_float * 3)(1, 1, 1), 0)
+    return renderer.SceneDesc(N, B, (ctypes.c_float * 3)(-1, -1, -1), extent, sigma, (ctypes.c_float * 3)(1, 1, 1), 0, 0)
 
 
 def test_workspace_bytes(lib):
@@ -63,8 +63,10 @@ def test_workspace_bytes(lib):
         assert got % 256 == 0
     neg = _desc()
     neg.max_steps = -1
+    badflag = _desc()
+    badflag.flags = 2
     for bad in [_desc(64, 6), _desc(60, 8), _desc(64, 8, extent=0.0), _desc(64, 8, sigma=float("nan")),
-                _desc(0, 8), _desc(64 * 1024, 8), _desc(8192, 4), neg]:
+                _desc(0, 8), _desc(64 * 1024, 8), _desc(8192, 4), neg, badflag]:
         assert lib.snerg_workspace_bytes(ctypes.byref(bad), 10) == 0
     assert lib.snerg_workspace_bytes(ctypes.byref(_desc()), -1) == 0
     assert lib.snerg_workspace_bytes(None, 1) == 0
@@ -101,7 +103,7 @@ def test_camera_record_layout():
     assert synth.CAMERA_DTYPE.fields["out_offset"][1] == 72
     assert synth.CAMERA_DTYPE.fields["W"][1] == 64
     assert ctypes.sizeof(renderer.RenderOpts) == 48
-    assert ctypes.sizeof(renderer.SceneDesc) == 44
+    assert ctypes.sizeof(renderer.SceneDesc) == 48
 
 
 def test_no_cpu_fallback_without_library(tmp_path, monkeypatch):

@@ -23,7 +23,7 @@ DEV = torch.device("cuda:0")
 
 def _desc(sc):
     return renderer.SceneDesc(sc.N, sc.B, (ctypes.c_float * 3)(*sc.bmin), float(sc.extent), float(sc.sigma_max),
-                              (ctypes.c_float * 3)(*sc.bg), 0)
+                              (ctypes.c_float * 3)(*sc.bg), 0, 0)
 
 
 def _noalloc_call(lib, sc, ind, atl, pix, mlp, out, status):
