@@ -169,6 +169,17 @@ snerg_status snerg_render_backward(snerg_handle h, const snerg_camera* cams, int
                                    const int32_t* d_fwd_counts, float* d_grad_atlas,
                                    float* d_grad_mlp, void* stream);
 
+/* Photometric loss of Eq. 3 over n rays: *d_loss += sum |C - C*|^2 (ACCUMULATED, caller
+ * zeroes; nullable), d_grad [n][3] = 2 (C - C*) (nullable). d_rgb, d_target: [n][3]. */
+snerg_status snerg_l2_loss(const float* d_rgb, const float* d_target, int64_t n, float* d_grad,
+                           float* d_loss, void* stream);
+
+/* One Adam step (the optimiser of the paper's fine-tuning, Sec. 5.5; learning rate 3e-4
+ * there) on n float32 parameters in place: m and v are the caller's moment buffers
+ * (zero before step 1), step counts from 1 (bias correction 1 - beta^step). */
+snerg_status snerg_adam_step(float* d_param, float* d_m, float* d_v, const float* d_grad, int64_t n,
+                             float lr, float beta1, float beta2, float eps, int32_t step, void* stream);
+
 /* Ray-list render for callers that cannot allocate device memory. The paper has no
  * counterpart: this entry point exists for callers such as a plug-in inside a host
  * application that owns all GPU memory through its own pool and forbids cudaMalloc, a

@@ -171,3 +171,34 @@ def ray(scene, cam, px: int, py: int):
     out = np.zeros(8, np.float32)
     hit = _lib().oracle_ray(int(scene.N), float(scene.extent), _p(bmin), _p(cf), int(px), int(py), _p(out))
     return bool(hit), out[0:3].copy(), out[3:6].copy(), float(out[6]), float(out[7])
+
+
+def adam_step(param, m, v, grad, step, lr=3e-4, betas=(0.9, 0.999), eps=1e-8):
+    """Reference Adam update in FP64 (Kingma & Ba), in place on numpy arrays; the
+    optimiser of the paper's fine-tuning (Sec. 5.5)."""
+    b1, b2 = betas
+    m *= b1
+    m += (1 - b1) * grad
+    v *= b2
+    v += (1 - b2) * grad * grad
+    mh = m / (1 - b1 ** step)
+    vh = v / (1 - b2 ** step)
+    param -= lr * mh / (np.sqrt(vh) + eps)
+    return param
+
+
+def finetune_steps(scene, pix, target, mlp, steps, lr=3e-4):
+    """`steps` fine-tuning steps of the MLP with the oracle's render and adjoint and the
+    reference Adam; returns (the parameter after each step, the loss before each step)."""
+    w = np.asarray(mlp, np.float64).copy()
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    params, losses = [], []
+    for t in range(1, steps + 1):
+        out = render_rays(scene, pix, mlp=w)
+        d = out["rgb"] - np.asarray(target, np.float64)
+        losses.append(float((d * d).sum()))
+        _, g = backward_rays(scene, pix, 2.0 * d, mlp=w, atlas_grad=False)
+        adam_step(w, m, v, g, t, lr)
+        params.append(w.copy())
+    return params, losses

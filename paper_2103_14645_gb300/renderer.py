@@ -27,7 +27,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error"
 EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_render_rays",
             "snerg_render_backward", "snerg_last_status", "snerg_launch_count",
             "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc",
-            "snerg_set_mlp"]
+            "snerg_set_mlp", "snerg_l2_loss", "snerg_adam_step"]
 
 
 class SnergError(RuntimeError):
@@ -81,6 +81,11 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_destroy.restype = None
     lib.snerg_status_str.argtypes = [ctypes.c_int]
     lib.snerg_status_str.restype = ctypes.c_char_p
+    lib.snerg_l2_loss.argtypes = [P, P, i64, P, P, P]
+    lib.snerg_l2_loss.restype = ctypes.c_int
+    lib.snerg_adam_step.argtypes = [P, P, P, P, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, i32, P]
+    lib.snerg_adam_step.restype = ctypes.c_int
     lib.snerg_set_mlp.argtypes = [P, P]
     lib.snerg_set_mlp.restype = ctypes.c_int
     lib.snerg_render_rays_noalloc.argtypes = [P, P, P, i64, P, i32, P, i64, P, P, P, P]
@@ -303,3 +308,55 @@ class SnergRenderFn(torch.autograd.Function):
 def render_rays_autograd(renderer: Renderer, cams, pix: torch.Tensor, mlp: torch.Tensor,
                          atlas_values: torch.Tensor) -> torch.Tensor:
     return SnergRenderFn.apply(mlp, atlas_values, renderer, cams, pix)
+
+
+def l2_loss(rgb: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None,
+            loss: torch.Tensor | None = None):
+    """Eq. 3 on the GPU (snerg_l2_loss): accumulates sum |C - C*|^2 into `loss` (float32
+    [1]) and writes dL/dC = 2 (C - C*) into `grad`."""
+    lib = load_library()
+    _require_cuda(rgb, "rgb", torch.float32)
+    _require_cuda(target, "target", torch.float32)
+    n = rgb.numel() // 3
+    _check(lib.snerg_l2_loss(_ptr(rgb), _ptr(target), n, _ptr(grad), _ptr(loss), _stream(rgb.device)),
+           "snerg_l2_loss")
+
+
+def adam_step(param: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, step: int,
+              lr: float = 3e-4, betas=(0.9, 0.999), eps: float = 1e-8):
+    """One in-place Adam step on the GPU (snerg_adam_step)."""
+    lib = load_library()
+    for t, name in ((param, "param"), (m, "m"), (v, "v"), (grad, "grad")):
+        _require_cuda(t, name, torch.float32)
+    _check(lib.snerg_adam_step(_ptr(param), _ptr(m), _ptr(v), _ptr(grad), param.numel(), float(lr), float(betas[0]),
+                               float(betas[1]), float(eps), int(step), _stream(param.device)), "snerg_adam_step")
+
+
+class FineTuner:
+    """Fine-tunes the view-dependence MLP of a baked grid against observed pixels with
+    Adam and the L2 loss, as the paper does after baking (Sec. 5.5: Adam, learning rate
+    3e-4). One step = render_rays (keeping per-ray state) -> loss and dL/dC -> backward
+    (dL/dPhi) -> Adam, all in the library's kernels."""
+
+    def __init__(self, renderer: Renderer, mlp, lr: float = 3e-4, betas=(0.9, 0.999), eps: float = 1e-8):
+        self.r = renderer
+        self.mlp = torch.as_tensor(np.asarray(mlp, np.float32)).to(renderer.device).contiguous()
+        self.m = torch.zeros_like(self.mlp)
+        self.v = torch.zeros_like(self.mlp)
+        self.grad = torch.zeros_like(self.mlp)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=renderer.device)
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.steps = 0
+
+    def step(self, cams, pix: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
+        """One Adam step on rays pix [n,3] with observed colours target [n,3]; returns the
+        loss before the step (a device tensor [1])."""
+        fwd = self.r.render_rays(cams, pix, self.mlp, aux=True, counts=True)
+        g = torch.empty_like(fwd["rgb"])
+        self.loss.zero_()
+        self.grad.zero_()
+        l2_loss(fwd["rgb"], target, g, self.loss)
+        self.r.backward(cams, pix, self.mlp, g, None, self.grad, fwd_aux=fwd["aux"], fwd_counts=fwd["counts"])
+        self.steps += 1
+        adam_step(self.mlp, self.m, self.v, self.grad, self.steps, self.lr, self.betas, self.eps)
+        return self.loss

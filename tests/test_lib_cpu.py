@@ -24,7 +24,7 @@ def lib():
 def declared_functions():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(snerg_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(snerg_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_declares_the_boundary():

@@ -452,3 +452,21 @@ def test_unpremultiply_gradient_matches_central_differences():
         mm[p] -= h
         fd = (_loss(sc, pix, target, val, mp)[0] - _loss(sc, pix, target, val, mm)[0]) / (2 * h)
         assert abs(fd - gmlp[p]) <= 1e-6 * max(1.0, abs(fd)), (p, fd, gmlp[p])
+
+
+def test_reference_adam_matches_torch():
+    """The FP64 reference Adam against torch.optim.Adam (library routine)."""
+    rng = np.random.default_rng(31)
+    p0 = rng.normal(size=50)
+    grads = rng.normal(size=(6, 50)) * np.logspace(-4, 1, 50)
+    w = p0.copy()
+    m = np.zeros(50)
+    v = np.zeros(50)
+    t = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([t], lr=3e-4, betas=(0.9, 0.999), eps=1e-8)
+    for k in range(6):
+        oracle.adam_step(w, m, v, grads[k], k + 1)
+        opt.zero_grad()
+        t.grad = torch.tensor(grads[k])
+        opt.step()
+    np.testing.assert_allclose(w, t.detach().numpy(), rtol=0, atol=1e-12)
