@@ -374,6 +374,12 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
                       "fwd_mrays_s": round(n / (np.mean(ms_f) * 1e-3) / 1e6, 3),
                       "fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3),
                       "ms_fwd": round(float(np.mean(ms_f)), 4), "ms_fwd_bwd": round(float(np.mean(ms_fb)), 4)}
+    # fine-tuning steps (Sec. 5.5): render -> L2 loss -> adjoint -> Adam, all in the library
+    ft = renderer.FineTuner(rb, wsc.mlp)
+    ms_ft = time_steps(lambda: ft.step(wsc.cameras, pix, tgt), reps, 2, stream, flush)
+    out["finetune"] = {"ms_per_step": round(float(np.mean(ms_ft)), 4),
+                       "mrays_s": round(n / (np.mean(ms_ft) * 1e-3) / 1e6, 3),
+                       "steps_per_s": round(1e3 / float(np.mean(ms_ft)), 1)}
     del rb, ga, gm
     if not args.no_large:
         out["large"] = large_section(args, dev, stream, flush)
