@@ -18,6 +18,10 @@
  *   * if any sample was composited, the tiny MLP (2 hidden layers of 16, Sec. 4.2)
  *     adds a view-dependent residual (Eq. 7): C = C_d + sigmoid(MLP(C_d, V, PE(d))),
  *     plus T_final * background (App. A evaluates the MLP only where alpha > 0);
+ *   * optional non-deferred comparison model (the per-sample ablation of Sec. 6): the same
+ *     MLP evaluated at every composited sample on that sample's own (c_d, v), the sample
+ *     colour c_d + sigmoid(MLP(c_d, v, PE(d))) composited with the same weights, no
+ *     per-pixel residual;
  *   * optional partial un-premultiply (App. C, forward-facing scenes): after compositing,
  *     (C_d, alpha, V) *= min(1, 1.5 alpha) / alpha where alpha = 1 - T_final > 0, so the
  *     MLP sees the scaled C_d and V and the background weight becomes 1 - min(1, 1.5 alpha);
@@ -76,6 +80,8 @@ typedef struct {
     double delta;          /* voxel width in world units, extent / N */
     int64_t max_iter;
     int unpremultiply;     /* App. C partial un-premultiply */
+    int per_sample_mlp;    /* non-deferred comparison model */
+    const double* mlp;     /* weights, for the per-sample model */
 } OScene;
 
 /* ------------------------------------------------------------------------- */
@@ -163,9 +169,13 @@ static ORay ray_setup(const OScene* S, const float* cam, int32_t px, int32_t py)
 typedef struct {
     double cd[3], v[4];
     double T;
+    double rgb_ps[3];      /* per-sample model: sum_k w_k (c_d,k + residual_k) */
     int32_t steps, active;
     int status;
 } OMarch;
+
+static void mlp_input(const double cd[3], const double v[4], const float d[3], double x[]);
+static double sample_residual(const double* w, const double x[], int c);
 
 static void march(const OScene* S, const ORay* r, uint64_t* trace, int32_t trace_cap,
                   const double* g_feat /* 7 adjoint values or NULL */, double* grad, OMarch* out) {
@@ -238,6 +248,18 @@ static void march(const OScene* S, const ORay* r, uint64_t* trace, int32_t trace
         double x = sigma * S->delta;
         double alpha = -expm1(-x);
         double wk = out->T * alpha;
+        if (S->per_sample_mlp) {
+            double cdk[3] = {0, 0, 0}, vk[4] = {0, 0, 0, 0}, x[34];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int c = 0; c < 2; ++c) {
+                        int32_t X = c ? c1[0] : c0[0], Y = b ? c1[1] : c0[1], Z = a ? c1[2] : c0[2];
+                        for (int ch = 0; ch < 3; ++ch) cdk[ch] += w64[a][b][c] * channel_value(S, X, Y, Z, 1 + ch);
+                        for (int ch = 0; ch < 4; ++ch) vk[ch] += w64[a][b][c] * channel_value(S, X, Y, Z, 4 + ch);
+                    }
+            mlp_input(cdk, vk, r->d, x);
+            for (int ch = 0; ch < 3; ++ch) out->rgb_ps[ch] += wk * (cdk[ch] + sample_residual(S->mlp, x, ch));
+        }
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
                 for (int c = 0; c < 2; ++c) {
@@ -315,6 +337,13 @@ static void mlp_forward(const double* w, const double x[MLP_IN], OMlp* m) {
     }
 }
 
+/* residual channel c of the MLP at input x (per-sample model) */
+static double sample_residual(const double* w, const double x[], int c) {
+    OMlp m;
+    mlp_forward(w, x, &m);
+    return m.res[c];
+}
+
 /* adjoint of mlp_forward: g_res -> grads of the weights (accumulated) and of the input */
 static void mlp_backward(const double* w, const double x[MLP_IN], const OMlp* m, const double g_res[MLP_OUT],
                          double* gw, double gx[MLP_IN]) {
@@ -364,7 +393,10 @@ static int scene_init(OScene* S, int32_t N, int32_t B, const float* bmin, float 
     S->kappa32 = (float)(sigma_max * ((double)extent / (double)N) / 255.0);
     S->taumax32 = (float)log(1000.0);
     S->max_iter = 4 * (int64_t)N + 16;
+    if ((flags & ~3) || (flags & 3) == 3) return OR_E_INVAL;   /* un-premultiply is a deferred-model option */
     S->unpremultiply = (flags & 1) != 0;
+    S->per_sample_mlp = (flags & 2) != 0;
+    S->mlp = NULL;
     for (int64_t i = 0; i < (int64_t)S->G * S->G * S->G; ++i)
         if (ind[i] < -1 || ind[i] >= nb) return OR_E_INVAL;
     return OR_OK;
@@ -381,6 +413,7 @@ int oracle_render_rays(int32_t N, int32_t B, const float* bmin, float extent, do
     OScene S;
     int st = scene_init(&S, N, B, bmin, extent, sigma_max, bg, ind, atlas, val, nb, flags);
     if (st) return st;
+    S.mlp = mlp;
     int err = 0;
     #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i) {
@@ -410,7 +443,12 @@ int oracle_render_rays(int32_t N, int32_t B, const float* bmin, float extent, do
             mlp_forward(mlp, x, &mm);
             for (int c = 0; c < 3; ++c) res[c] = mm.res[c];
         }
-        for (int c = 0; c < 3; ++c) rgb[3 * i + c] = (m.active > 0 ? m.cd[c] + res[c] : 0.0) + m.T * S.bg[c];
+        for (int c = 0; c < 3; ++c) {
+            if (S.per_sample_mlp)
+                rgb[3 * i + c] = m.rgb_ps[c] + m.T * S.bg[c];
+            else
+                rgb[3 * i + c] = (m.active > 0 ? m.cd[c] + res[c] : 0.0) + m.T * S.bg[c];
+        }
         if (aux) {       /* the composites before any un-premultiply */
             for (int c = 0; c < 3; ++c) aux[8 * i + c] = raw_cd[c];
             for (int c = 0; c < 4; ++c) aux[8 * i + 3 + c] = raw_v[c];
@@ -432,6 +470,7 @@ int oracle_backward_rays(int32_t N, int32_t B, const float* bmin, float extent, 
     OScene S;
     int st = scene_init(&S, N, B, bmin, extent, sigma_max, bg, ind, atlas, val, nb, flags);
     if (st) return st;
+    if (S.per_sample_mlp) return OR_E_INVAL;   /* comparison model: forward only */
     int err = 0;
     #pragma omp parallel
     {

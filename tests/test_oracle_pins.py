@@ -470,3 +470,90 @@ def test_reference_adam_matches_torch():
         t.grad = torch.tensor(grads[k])
         opt.step()
     np.testing.assert_allclose(w, t.detach().numpy(), rtol=0, atol=1e-12)
+
+
+
+# --------------------------------------------------------------------------------------
+# non-deferred comparison model (the per-sample ablation): the MLP at every composited
+# sample on that sample's own (c_d, v)
+# --------------------------------------------------------------------------------------
+
+PER_SAMPLE = 2
+
+
+def test_per_sample_zero_weights_give_half_the_opacity():
+    """W = 0, b = 0: every composited sample adds 1/2 * w_k, so C = C_d + acc/2 + T bg
+    (the deferred model adds 1/2 once: C_d + 1/2 + T bg)."""
+    sc = synth.make_scene("tiny")
+    sc.flags = PER_SAMPLE
+    out = oracle.render_rays(sc, _pix(sc), mlp=np.zeros(synth.MLP_NPARAM, np.float32))
+    acc = out["aux"][:, 7]
+    np.testing.assert_allclose(out["rgb"], out["aux"][:, :3] + 0.5 * acc[:, None] + (1 - acc)[:, None],
+                               rtol=0, atol=1e-14)
+    assert (acc > 0.05).any()
+
+
+def test_per_sample_silent_mlp_equals_deferred():
+    sc = synth.make_scene("tiny")
+    a = oracle.render_rays(sc, _pix(sc), mlp=helpers.silent_mlp())
+    sc.flags = PER_SAMPLE
+    b = oracle.render_rays(sc, _pix(sc), mlp=helpers.silent_mlp())
+    np.testing.assert_allclose(b["rgb"], a["rgb"], rtol=0, atol=1e-14)
+
+
+def test_per_sample_uniform_slab_closed_form():
+    """A uniform slab: every sample has the same input, so C = (c + r)(1 - T) + T bg with
+    r = sigmoid(MLP(c, v, PE(d))) from torch float64 linear layers."""
+    col = np.array([100, 150, 200, 10, 20, 30, 40])
+    rng = np.random.default_rng(41)
+    w = synth.init_mlp(rng)
+    sc = helpers.slab_scene(z_range=(4, 6), q=200, color=col, sigma_max_vox=1.0, mlp=w)
+    sc.flags = PER_SAMPLE
+    out = oracle.render_rays(sc, np.array([[0, 0, 0]]))
+    T = math.exp(-2 * 200 / 255.0)
+    d = np.array([0.0, 0.0, -1.0])
+    pe = [col[:3] / 255.0, col[3:] / 255.0, d]
+    for l in range(4):
+        pe += [np.sin(2.0 ** l * d), np.cos(2.0 ** l * d)]
+    res = _torch_mlp(w, np.concatenate(pe)[None])[0]
+    np.testing.assert_allclose(out["rgb"][0], (col[:3] / 255.0 + res) * (1 - T) + T, rtol=0, atol=1e-13)
+
+
+def test_per_sample_brute_force():
+    sc = synth.make_scene("tiny")
+    sc.flags = PER_SAMPLE
+    dense = helpers.blocks_to_dense(sc)
+    from scipy.ndimage import map_coordinates
+    rng = np.random.default_rng(6)
+    pix = np.stack([np.zeros(40, int), rng.integers(0, 24, 40), rng.integers(0, 20, 40)], 1)
+    out = oracle.render_rays(sc, pix)
+    N, B = sc.N, sc.B
+    chans = [dense[..., c].astype(np.float64) / 255.0 for c in range(8)]
+    sigma_max = float(np.float32(sc.sigma_max))
+    delta = float(np.float32(sc.extent)) / N
+    for i, (c, x, y) in enumerate(pix):
+        hit, o, d, ts, te = oracle.ray(sc, sc.cameras[c], x, y)
+        T, tau, rgb, k = 1.0, 0.0, np.zeros(3), 0
+        while hit:
+            tk = np.float32(ts) + (np.float32(k) + np.float32(0.5))
+            k += 1
+            if not tk < np.float32(te):
+                break
+            u = np.asarray(o, np.float32) + np.float32(tk) * np.asarray(d, np.float32)
+            j = np.clip(np.floor(u).astype(np.int64), 0, N - 1)
+            if sc.ind[j[2] // B, j[1] // B, j[0] // B] < 0 or dense[j[2], j[1], j[0], 0] == 0:
+                continue
+            coord = (np.asarray(u[::-1], np.float64) - 0.5).reshape(3, 1)
+            v = [map_coordinates(ch, coord, order=1, mode="nearest")[0] for ch in chans]
+            sd = v[0] * sigma_max * delta
+            wk = T * (1 - math.exp(-sd))
+            dd = np.asarray(d, np.float64)
+            pe = [np.array(v[1:4]), np.array(v[4:8]), dd]
+            for l in range(4):
+                pe += [np.sin(2.0 ** l * dd), np.cos(2.0 ** l * dd)]
+            rgb += wk * (np.array(v[1:4]) + _torch_mlp(sc.mlp, np.concatenate(pe)[None])[0])
+            T *= math.exp(-sd)
+            tau += sd
+            if tau > math.log(1000.0):
+                break
+        np.testing.assert_allclose(out["rgb"][i], rgb + T * np.asarray(sc.bg), rtol=0, atol=1e-10)
