@@ -288,6 +288,18 @@ def run_ours(args, ws, rank, local):
     extra = {}
     if not args.no_extra:
         extra = extra_sections(args, r, sc, dev, stream, flush, barrier)
+        # the non-deferred comparison model on the same view (the paper's per-sample
+        # ablation): the view-dependence MLP at every composited sample
+        from paper_2103_14645_gb300 import synth as _synth
+        ps_scene = _synth.custom_scene(sc.N, sc.B, sc.ind, sc.atlas, sc.sigma_max, sc.mlp, sc.cameras,
+                                       flags=renderer.FLAG_PER_SAMPLE_MLP)
+        rps = renderer.Renderer.from_scene(ps_scene, dev)
+        rps.set_mlp(sc.mlp)
+        ms_ps = time_steps(lambda: rps.render(cams, None, out=out), max(3, min(args.steps, 10)), 2, stream, flush)
+        extra["per_sample_mlp"] = {"ms_per_frame": round(float(np.mean(ms_ps)), 4),
+                                   "mrays_s": round(n_rays / (np.mean(ms_ps) * 1e-3) / 1e6, 3),
+                                   "slowdown_vs_deferred": round(float(np.mean(ms_ps)) / t_step, 3)}
+        del rps
     clocks = sampler.stop()
 
     if rank != 0:

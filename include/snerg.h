@@ -71,6 +71,12 @@ typedef struct {
  * sees the scaled C_d and V and the background weight is 1 - min(1, 1.5 alpha). The aux
  * output keeps the composites before scaling. */
 #define SNERG_FLAG_UNPREMULTIPLY 1
+/* The non-deferred comparison model (the paper's per-sample ablation, Sec. 6): the
+ * view-dependence MLP is evaluated at every composited sample on that sample's own
+ * (c_d, v) and the sample colours c_d + residual are composited; there is no per-pixel
+ * residual. Forward only, one-camera launches only (snerg_render without persistent;
+ * other entry points return SNERG_E_UNSUPPORTED); not combinable with UNPREMULTIPLY. */
+#define SNERG_FLAG_PER_SAMPLE_MLP 2
 
 /* Pinhole camera (Sec. 4.1 r(t) = o + t d). 80 bytes, host memory.
  * Pixel (x, y) looks along R (x + 0.5 - cx) / fx, -(y + 0.5 - cy) / fy, -1) normalised,

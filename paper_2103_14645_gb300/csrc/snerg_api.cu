@@ -48,7 +48,8 @@ bool desc_ok(const snerg_scene_desc* d) {
     if (!(std::isfinite(d->extent) && d->extent > 0.0f)) return false;
     if (!(std::isfinite(d->sigma_max) && d->sigma_max >= 0.0f)) return false;
     if (d->max_steps < 0) return false;
-    if (d->flags & ~SNERG_FLAG_UNPREMULTIPLY) return false;
+    if (d->flags & ~(SNERG_FLAG_UNPREMULTIPLY | SNERG_FLAG_PER_SAMPLE_MLP)) return false;
+    if ((d->flags & SNERG_FLAG_UNPREMULTIPLY) && (d->flags & SNERG_FLAG_PER_SAMPLE_MLP)) return false;
     return finite3(d->bmin) && finite3(d->bg);
 }
 
@@ -382,8 +383,10 @@ extern "C" snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, i
     if (!d_rgb || (!d_mlp && !h->has_w)) return SNERG_E_INVAL;
     const MlpWeights* pw = d_mlp ? nullptr : &h->host_w;
     cudaStream_t st = (cudaStream_t)stream;
-    if (opts && opts->persistent && !opts_debug(opts))
+    if (opts && opts->persistent && !opts_debug(opts)) {
+        if (h->desc.flags & SNERG_FLAG_PER_SAMPLE_MLP) return SNERG_E_UNSUPPORTED;
         return render_persistent(h, cams, n_cams, d_mlp, pw, d_rgb, opts, st);
+    }
     const DebugOut dbg = make_dbg(opts);
     for (int i = 0; i < n_cams; ++i) {
         if (cams[i].W == 0 || cams[i].H == 0) continue;
@@ -408,6 +411,7 @@ extern "C" snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* ca
                                           const int32_t* d_pix, int64_t n, const float* d_mlp, float* d_rgb,
                                           const snerg_render_opts* opts, void* stream) {
     if (!h || n < 0) return SNERG_E_INVAL;
+    if (h->desc.flags & SNERG_FLAG_PER_SAMPLE_MLP) return SNERG_E_UNSUPPORTED;
     CamTable* t = new (std::nothrow) CamTable;
     if (!t) return SNERG_E_NOMEM;
     if (!make_table(cams, n_cams, t)) { delete t; return SNERG_E_INVAL; }
@@ -427,6 +431,7 @@ extern "C" snerg_status snerg_render_backward(snerg_handle h, const snerg_camera
                                               const int32_t* d_fwd_counts, float* d_grad_atlas, float* d_grad_mlp,
                                               void* stream) {
     if (!h || n < 0) return SNERG_E_INVAL;
+    if (h->desc.flags & SNERG_FLAG_PER_SAMPLE_MLP) return SNERG_E_UNSUPPORTED;
     CamTable* t = new (std::nothrow) CamTable;
     if (!t) return SNERG_E_NOMEM;
     if (!make_table(cams, n_cams, t)) { delete t; return SNERG_E_INVAL; }

@@ -21,7 +21,7 @@ struct ImageTile {
     static constexpr int TW = 8 * WX, TH = 4 * WY;  // CTA tile in pixels
 };
 
-template <bool DBG, bool PW, int NW>
+template <bool DBG, bool PW, int NW, bool PS>
 __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const DevScene s, const snerg_camera cam,
                                                                         const float* __restrict__ mlp,
                                                                         const __grid_constant__ MlpWeights pw,
@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const De
         load_mlp_smem_t(sW, mlp);
         __syncthreads();
     }
+    const MlpWeights* pwp = PW ? &pw : nullptr;
     using T = ImageTile<NW>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = blockIdx.x * T::TW + (warp % T::WX) * 8 + (lane & 7);
@@ -41,13 +42,13 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const De
     MarchState st;
     int k_first = 0;
     if (DBG && dbg.trace)
-        march<true, false>(s, r, st, dbg.trace + pix * dbg.trace_cap, dbg.trace_cap, nullptr, nullptr, 0,
-                           &k_first);
+        march<true, false, PS>(s, r, st, dbg.trace + pix * dbg.trace_cap, dbg.trace_cap, nullptr, nullptr, 0,
+                               &k_first, pwp, sW);
     else
-        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr, 0, DBG ? &k_first : nullptr);
+        march<false, false, PS>(s, r, st, nullptr, 0, nullptr, nullptr, 0, DBG ? &k_first : nullptr, pwp, sW);
     record_status(s, st);
     float c[3], aux[kAuxCh];
-    finish_ray(s, sW, nullptr, r, st, c, aux, PW ? &pw : nullptr);
+    finish_ray(s, sW, nullptr, r, st, c, aux, pwp);
     rgb[pix * 3 + 0] = c[0];
     rgb[pix * 3 + 1] = c[1];
     rgb[pix * 3 + 2] = c[2];
@@ -161,28 +162,35 @@ __global__ void __launch_bounds__(128, 8) render_persistent_kernel(const DevScen
     }
 }
 
+constexpr int kImageWarps = 4;     // warps per CTA of the one-camera launch
+
 static const MlpWeights& no_weights() {
     static const MlpWeights z = {};
     return z;
 }
 
-constexpr int kImageWarps = 4;     // warps per CTA of the one-camera launch
-
-cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
-                                float* rgb, const DebugOut& dbg, cudaStream_t st) {
-    if (cam.W <= 0 || cam.H <= 0) return cudaSuccess;
+template <bool PS>
+static void image_launch(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
+                         float* rgb, const DebugOut& dbg, cudaStream_t st) {
     using T = ImageTile<kImageWarps>;
     dim3 grid((cam.W + T::TW - 1) / T::TW, (cam.H + T::TH - 1) / T::TH);
     const int nt = 32 * kImageWarps;
     const bool d = dbg.aux || dbg.counts || dbg.trace;
     const MlpWeights& w = pw ? *pw : no_weights();
     if (pw) {
-        if (d) render_image_kernel<true, true, kImageWarps><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
-        else render_image_kernel<false, true, kImageWarps><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        if (d) render_image_kernel<true, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        else render_image_kernel<false, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
     } else {
-        if (d) render_image_kernel<true, false, kImageWarps><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
-        else render_image_kernel<false, false, kImageWarps><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        if (d) render_image_kernel<true, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        else render_image_kernel<false, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
     }
+}
+
+cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
+                                float* rgb, const DebugOut& dbg, cudaStream_t st) {
+    if (cam.W <= 0 || cam.H <= 0) return cudaSuccess;
+    if (s.flags & SNERG_FLAG_PER_SAMPLE_MLP) image_launch<true>(s, cam, mlp, pw, rgb, dbg, st);
+    else image_launch<false>(s, cam, mlp, pw, rgb, dbg, st);
     return cudaGetLastError();
 }
 

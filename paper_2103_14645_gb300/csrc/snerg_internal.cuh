@@ -96,6 +96,7 @@ struct Ray {
 
 struct MarchState {
     float acc[7];     // sum_k w_k * (sum_corners tw * code) for channels 1..7 (codes, not /255)
+    float rgb_ps[3];  // non-deferred comparison model: sum_k w_k (c_d,k + residual_k)
     float T;
     float tau;
     int steps;
@@ -276,13 +277,22 @@ __device__ __forceinline__ void accumulate_colour(MarchState& st, const uint2 cv
 // k_begin: first lattice index to consider (0, or a k known to precede every composited
 // sample, in which case the result is the same); k_first (nullable) receives the index
 // of the first composited sample (kmax if none).
-template <bool TRACE, bool GRAD>
+struct MlpWeights;
+__device__ __forceinline__ void per_sample_residual(const MlpWeights* pw, const float* sW, const float cd[3],
+                                                    const float v[4], const float d[3], float res[3]);
+
+// PS: the non-deferred comparison model (SNERG_FLAG_PER_SAMPLE_MLP): every composited
+// sample also evaluates the view-dependence MLP on its own (c_d, v) (weights from pw, else
+// from sW) and adds w_k (c_d,k + residual_k) to st.rgb_ps.
+template <bool TRACE, bool GRAD, bool PS = false>
 __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchState& st,
                                       uint64_t* trace, int trace_cap,
                                       const float* gfeat, float* grad_atlas,
-                                      int k_begin = 0, int* k_first = nullptr) {
+                                      int k_begin = 0, int* k_first = nullptr,
+                                      const MlpWeights* ps_w = nullptr, const float* ps_sw = nullptr) {
 #pragma unroll
     for (int c = 0; c < 7; ++c) st.acc[c] = 0.0f;
+    st.rgb_ps[0] = st.rgb_ps[1] = st.rgb_ps[2] = 0.0f;
     st.T = 1.0f;
     st.tau = 0.0f;
     st.steps = 0;
@@ -397,6 +407,28 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             const float wk = st.T * (1.0f - e);
             st.T *= e;
             accumulate_colour(st, cv, wk, f, g);
+            if (PS) {
+                // this sample's own decoded colour and features, then its residual
+                float ck[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float tw = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
+                    ck[0] = fmaf(tw, code(cv[c].x, 1), ck[0]);
+                    ck[1] = fmaf(tw, code(cv[c].x, 2), ck[1]);
+                    ck[2] = fmaf(tw, code(cv[c].x, 3), ck[2]);
+                    ck[3] = fmaf(tw, code(cv[c].y, 0), ck[3]);
+                    ck[4] = fmaf(tw, code(cv[c].y, 1), ck[4]);
+                    ck[5] = fmaf(tw, code(cv[c].y, 2), ck[5]);
+                    ck[6] = fmaf(tw, code(cv[c].y, 3), ck[6]);
+                }
+                const float inv255 = 1.0f / 255.0f;
+                const float cdk[3] = {ck[0] * inv255, ck[1] * inv255, ck[2] * inv255};
+                const float vk[4] = {ck[3] * inv255, ck[4] * inv255, ck[5] * inv255, ck[6] * inv255};
+                float res[3];
+                per_sample_residual(ps_w, ps_sw, cdk, vk, r.d, res);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) st.rgb_ps[c] = fmaf(wk, cdk[c] + res[c], st.rgb_ps[c]);
+            }
             if (GRAD) {
                 float tw[8];
 #pragma unroll
@@ -679,6 +711,12 @@ __device__ __forceinline__ void mlp_residual_param(const MlpWeights& W, const fl
     }
 }
 
+__device__ __forceinline__ void per_sample_residual(const MlpWeights* pw, const float* sW, const float cd[3],
+                                                    const float v[4], const float d[3], float res[3]) {
+    if (pw) mlp_residual_param(*pw, cd, v, d, res);
+    else mlp_residual_regs(sW, cd, v, d, res);
+}
+
 // Finish one ray: colour = C_d + residual + T bg (residual only if something was
 // composited). sW: weights in the transposed layout of load_mlp_smem_t; xrow: this
 // thread's kXStride-float row of shared memory to stage the MLP input in, or nullptr to
@@ -707,7 +745,10 @@ __device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, f
         T = 1.0f - (1.0f - st.T) * sc;
     }
     float res[3] = {0.0f, 0.0f, 0.0f};
-    if (st.active > 0) {
+    if (s.flags & SNERG_FLAG_PER_SAMPLE_MLP) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res[c] = st.rgb_ps[c];
+    } else if (st.active > 0) {
         float m[3];
         if (pw) {
             mlp_residual_param(*pw, cd, v, r.d, m);

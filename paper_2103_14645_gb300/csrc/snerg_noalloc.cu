@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(128, 8) render_rays_noalloc_kernel(const DevSc
 
 bool desc_ok_noalloc(const snerg_scene_desc* d) {
     if (!d || d->N < 1 || d->N > 16384 || d->B < 2 || d->B > 64 || (d->B & (d->B - 1)) || d->N % d->B) return false;
-    if (d->max_steps < 0 || (d->flags & ~SNERG_FLAG_UNPREMULTIPLY)) return false;
+    if (d->max_steps < 0 || (d->flags & ~SNERG_FLAG_UNPREMULTIPLY)) return false;   // deferred model only
     if (!(d->extent > 0.0f) || !(d->extent < INFINITY) || !(d->sigma_max >= 0.0f) || !(d->sigma_max < INFINITY))
         return false;
     for (int i = 0; i < 3; ++i)

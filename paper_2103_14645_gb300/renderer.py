@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsnerg.so")
 MLP_PARAMS = 883
 FLAG_UNPREMULTIPLY = 1
+FLAG_PER_SAMPLE_MLP = 2
 MAX_CAMERAS = 256
 AUX_CH = 8
 

@@ -548,3 +548,59 @@ def test_unpremultiply_backward_parity():
     r.check_status()
     assert np.abs(ga2.cpu().numpy() - ra).max() <= 1e-4 * np.abs(ra).max()
     assert np.abs(gm2.cpu().numpy() - rm).max() <= 1e-4 * np.abs(rm).max()
+
+
+# --------------------------------------------------------------------------------------
+# non-deferred comparison model (per-sample view-dependence MLP)
+# --------------------------------------------------------------------------------------
+
+def _per_sample(name):
+    sc0 = scene(name)
+    return synth.custom_scene(sc0.N, sc0.B, sc0.ind, sc0.atlas, sc0.sigma_max, sc0.mlp, sc0.cameras,
+                              flags=renderer.FLAG_PER_SAMPLE_MLP)
+
+
+@pytest.mark.parametrize("param_weights", [False, True])
+def test_per_sample_model_parity(param_weights):
+    sc = _per_sample("gauss64")
+    r = renderer.Renderer.from_scene(sc, DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    if param_weights:
+        r.set_mlp(sc.mlp)
+    out = r.render(sc.cameras, None if param_weights else w, counts=True, aux=True)
+    r.check_status()
+    o = oracle_all(sc)
+    np.testing.assert_array_equal(out["counts"].cpu().numpy()[:, :2], o["counts"])
+    assert np.abs(out["rgb"].cpu().numpy() - o["rgb"]).max() <= TOL
+    deferred = oracle_all(scene("gauss64"))
+    assert np.abs(o["rgb"] - deferred["rgb"]).max() > 1e-2
+
+
+def test_per_sample_model_paper_scale_view_sampled():
+    sc = _per_sample("shell1024")
+    r = renderer.Renderer.from_scene(sc, DEV)
+    r.set_mlp(sc.mlp)
+    img = r.render(sc.cameras, None).cpu().numpy()
+    r.check_status()
+    pix = synth.random_pixels(np.random.default_rng(44), sc.cameras, 4096)
+    o = oracle.render_rays(sc, pix)
+    idx = pix[:, 2].astype(np.int64) * 800 + pix[:, 1]
+    assert np.abs(img[idx] - o["rgb"]).max() <= TOL
+
+
+def test_per_sample_model_unsupported_paths():
+    sc = _per_sample("tiny")
+    r = renderer.Renderer.from_scene(sc, DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    pix = torch.zeros((4, 3), dtype=torch.int32, device=DEV)
+    for call in (lambda: r.render(sc.cameras, w, persistent=True, tile=(8, 4), ctas_per_sm=2),
+                 lambda: r.render_rays(sc.cameras, pix, w),
+                 lambda: r.backward(sc.cameras, pix, w, torch.zeros((4, 3), device=DEV), None,
+                                    torch.zeros(883, device=DEV))):
+        with pytest.raises(renderer.SnergError) as e:
+            call()
+        assert e.value.code == 5
+    sc0 = scene("tiny")
+    with pytest.raises((ValueError, renderer.SnergError)):
+        renderer.Renderer(sc0.N, sc0.B, sc0.bmin, sc0.extent, sc0.sigma_max, sc0.bg,
+                          torch.from_numpy(sc0.ind).to(DEV), torch.from_numpy(sc0.atlas).to(DEV), flags=3)

@@ -64,9 +64,11 @@ def test_workspace_bytes(lib):
     neg = _desc()
     neg.max_steps = -1
     badflag = _desc()
-    badflag.flags = 2
+    badflag.flags = 4                # undefined bit
+    combo = _desc()
+    combo.flags = 3                  # un-premultiply belongs to the deferred model
     for bad in [_desc(64, 6), _desc(60, 8), _desc(64, 8, extent=0.0), _desc(64, 8, sigma=float("nan")),
-                _desc(0, 8), _desc(64 * 1024, 8), _desc(8192, 4), neg, badflag]:
+                _desc(0, 8), _desc(64 * 1024, 8), _desc(8192, 4), neg, badflag, combo]:
         assert lib.snerg_workspace_bytes(ctypes.byref(bad), 10) == 0
     assert lib.snerg_workspace_bytes(ctypes.byref(_desc()), -1) == 0
     assert lib.snerg_workspace_bytes(None, 1) == 0
