@@ -8,7 +8,8 @@ of the method's arithmetic, and this wrapper reads scenes from it by attribute o
 
 The arithmetic lives in `snerg_oracle.c` (plain C, FP64 colour arithmetic, binary32
 integer decisions in a fixed operation order, `-ffp-contract=off`); every function there
-cites the paper passage it follows (Sec. 4.2 Eqs. 2, 5-7; Sec. 5.1-5.2; App. A; Sec. 5.5).
+cites the paper passage it follows (Sec. 4.2 Eqs. 2, 5-7; Sec. 5.1-5.2; App. A; Sec. 5.5;
+the bake of Sec. 5.3-5.4).
 
 Parity pins (tests/test_oracle_pins.py) tie it to closed forms, invariants, library
 routines and brute force on tiny grids. No function here is "parity unpinned".
@@ -59,6 +60,8 @@ def _lib():
         lib.oracle_mlp_input.restype = None
         lib.oracle_ray.argtypes = [i32, f32, P, P, i32, i32, P]
         lib.oracle_ray.restype = ctypes.c_int
+        lib.oracle_bake.argtypes = [i32, i32, P, f32, f32, f32, i32, P, P, P, P, P, i64, P]
+        lib.oracle_bake.restype = ctypes.c_int64
         _LIB = lib
     return _LIB
 
@@ -202,3 +205,23 @@ def finetune_steps(scene, pix, target, mlp, steps, lr=3e-4):
         adam_step(w, m, v, g, t, lr)
         params.append(w.copy())
     return params, losses
+
+
+def bake(N, B, bmin, extent, sigma_max, blobs, colors, jitter, tau_alpha=0.005, max_blocks=None):
+    """FP64 bake of the analytic field (Sec. 5.3): returns (ind [G,G,G] int32,
+    atlas [nb,B,B,B,8] uint8, block max alpha [G,G,G] f64)."""
+    G = N // B
+    blobs = np.ascontiguousarray(blobs, np.float32).reshape(-1, 5)
+    colors = np.ascontiguousarray(colors, np.float32).reshape(7, 4)
+    jitter = np.ascontiguousarray(jitter, np.float32).reshape(16, 3)
+    bmin = np.asarray(bmin, np.float32)
+    max_blocks = G ** 3 if max_blocks is None else max_blocks
+    ind = np.zeros((G, G, G), np.int32)
+    atlas = np.zeros((max_blocks, B, B, B, 8), np.uint8)
+    amax = np.zeros((G, G, G), np.float64)
+    nb = _lib().oracle_bake(int(N), int(B), _p(bmin), float(np.float32(extent)), float(np.float32(sigma_max)),
+                            float(np.float32(tau_alpha)), blobs.shape[0], _p(blobs), _p(colors), _p(jitter),
+                            _p(ind), _p(atlas), int(max_blocks), _p(amax))
+    if nb < 0:
+        raise OracleError("more kept blocks than max_blocks")
+    return ind, atlas[:nb].copy(), amax

@@ -27,7 +27,11 @@
  *     MLP sees the scaled C_d and V and the background weight becomes 1 - min(1, 1.5 alpha);
  *   * the backward pass is the exact adjoint of the above w.r.t. the decoded colour and
  *     feature values and the MLP weights, with density frozen (Sec. 5.5 fine-tunes the
- *     per-pixel network against an L2 image loss, Eq. 3).
+ *     per-pixel network against an L2 image loss, Eq. 3);
+ *   * baking (Sec. 5.3) of an analytic field that stands in for the trained network:
+ *     alpha = 1 - exp(-sigma v) at voxel centres, blocks with max alpha < tau_alpha
+ *     culled, 16 Gaussian-jittered samples per kept voxel averaged, 8-bit codes
+ *     (Sec. 5.4), kept blocks packed in raster order.
  *
  * Method decisions that the paper leaves open are taken as follows and are part of the
  * definition this oracle states (they fix which integer decisions are made):
@@ -536,4 +540,92 @@ int oracle_ray(int32_t N, float extent, const float* bmin, const float* cam, int
     out_f[6] = r.t_start;
     out_f[7] = r.t_end;
     return r.hit;
+}
+
+
+/* ------------------------------------------------------------------------- */
+/* Baking (Sec. 5.3) of an analytic field standing in for the trained network:  */
+/* dense evaluation at voxel centres, alpha = 1 - exp(-sigma v), macroblock      */
+/* culling at max alpha < tau_alpha, 16 Gaussian-jittered samples per voxel      */
+/* (std v / sqrt 12, offsets given by the caller) averaged, 8-bit quantisation   */
+/* (Sec. 5.4), packing in raster order of the kept blocks.                       */
+/* Field: sigma(x) = sum_i peak_i exp(-|x - c_i|^2 / (2 s_i^2)) (blob[i] = c, s,  */
+/* peak; world units); channel c (1..7) = 0.5 + 0.5 sin(w_c . x + phi_c).         */
+
+static double field_sigma(const float* blob, int nb, double x, double y, double z) {
+    double acc = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        const float* b = blob + 5 * i;
+        double dx = x - b[0], dy = y - b[1], dz = z - b[2];
+        acc += (double)b[4] * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * (double)b[3] * (double)b[3]));
+    }
+    return acc;
+}
+
+static double field_channel(const float* col, int c, double x, double y, double z) {
+    const float* w = col + 4 * c;
+    return 0.5 + 0.5 * sin((double)w[0] * x + (double)w[1] * y + (double)w[2] * z + (double)w[3]);
+}
+
+static uint8_t quant8(double v) {
+    if (!(v > 0.0)) return 0;
+    if (v >= 1.0) return 255;
+    return (uint8_t)floor(v * 255.0 + 0.5);
+}
+
+/* Outputs: ind[G^3] (-1 or slot), atlas[max_blocks][B^3][8]; returns the number of
+ * kept blocks (or -1 if more than max_blocks), and per-block maximum alpha in
+ * block_alpha[G^3] (for diagnosing threshold ties). */
+int64_t oracle_bake(int32_t N, int32_t B, const float* bmin, float extent, float sigma_max, float tau_alpha,
+                    int32_t n_blob, const float* blob, const float* color, const float* jitter /*[16][3]*/,
+                    int32_t* ind, uint8_t* atlas, int64_t max_blocks, double* block_alpha) {
+    const int32_t G = N / B;
+    const double v = (double)extent / (double)N;
+    const int64_t G3 = (int64_t)G * G * G;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < G3; ++b) {
+        int32_t bx = (int32_t)(b % G), by = (int32_t)((b / G) % G), bz = (int32_t)(b / ((int64_t)G * G));
+        double amax = 0.0;
+        for (int32_t z = 0; z < B; ++z)
+            for (int32_t y = 0; y < B; ++y)
+                for (int32_t x = 0; x < B; ++x) {
+                    double px = bmin[0] + ((bx * B + x) + 0.5) * v;
+                    double py = bmin[1] + ((by * B + y) + 0.5) * v;
+                    double pz = bmin[2] + ((bz * B + z) + 0.5) * v;
+                    double a = -expm1(-field_sigma(blob, n_blob, px, py, pz) * v);
+                    if (a > amax) amax = a;
+                }
+        block_alpha[b] = amax;
+    }
+    int64_t nb = 0;
+    for (int64_t b = 0; b < G3; ++b) {
+        if (block_alpha[b] >= (double)tau_alpha) {
+            if (nb >= max_blocks) return -1;
+            ind[b] = (int32_t)nb++;
+        } else {
+            ind[b] = -1;
+        }
+    }
+    const int64_t vox = (int64_t)B * B * B;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < G3; ++b) {
+        if (ind[b] < 0) continue;
+        int32_t bx = (int32_t)(b % G), by = (int32_t)((b / G) % G), bz = (int32_t)(b / ((int64_t)G * G));
+        for (int32_t z = 0; z < B; ++z)
+            for (int32_t y = 0; y < B; ++y)
+                for (int32_t x = 0; x < B; ++x) {
+                    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    for (int sidx = 0; sidx < 16; ++sidx) {
+                        double px = bmin[0] + ((bx * B + x) + 0.5 + jitter[3 * sidx]) * v;
+                        double py = bmin[1] + ((by * B + y) + 0.5 + jitter[3 * sidx + 1]) * v;
+                        double pz = bmin[2] + ((bz * B + z) + 0.5 + jitter[3 * sidx + 2]) * v;
+                        acc[0] += field_sigma(blob, n_blob, px, py, pz);
+                        for (int c = 0; c < 7; ++c) acc[1 + c] += field_channel(color, c, px, py, pz);
+                    }
+                    uint8_t* out = atlas + ((int64_t)ind[b] * vox + ((int64_t)z * B + y) * B + x) * 8;
+                    out[0] = quant8(acc[0] / 16.0 / (double)sigma_max);
+                    for (int c = 0; c < 7; ++c) out[1 + c] = quant8(acc[1 + c] / 16.0);
+                }
+    }
+    return nb;
 }
