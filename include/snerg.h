@@ -215,6 +215,50 @@ snerg_status snerg_render_rays_noalloc(const snerg_scene_desc* desc, const int32
                                        const int32_t* d_pix, int64_t n, const float* d_mlp,
                                        float* d_rgb, int32_t* d_status, void* stream);
 
+/* Largest number of density blobs of an analytic bake field. */
+#define SNERG_BAKE_MAX_BLOBS 64
+
+/* An analytic radiance field that stands in for the trained network when baking
+ * (Sec. 5.3). HOST memory, read during the call only. World units throughout.
+ *   density sigma(x) = sum_i peak_i exp(-|x - c_i|^2 / (2 s_i^2)),
+ *                      blob[i] = {c_x, c_y, c_z, s_i > 0, peak_i >= 0};
+ *   channel c of (diffuse r, g, b, f0..f3) = 0.5 + 0.5 sin(w_c . x + phi_c),
+ *                      color[c] = {w_x, w_y, w_z, phi}. */
+typedef struct {
+    int32_t n_blob;                            /* 0..SNERG_BAKE_MAX_BLOBS */
+    float tau_alpha;                           /* culling threshold, in (0, 1); paper: 0.005 */
+    float blob[SNERG_BAKE_MAX_BLOBS][5];
+    float color[7][4];
+    float jitter[16][3];                       /* offsets of the 16 anti-aliasing samples in
+                                                  voxel units (the paper draws them from a
+                                                  Gaussian of std 1/sqrt(12) voxels), same for
+                                                  every voxel; |offset| <= 8 */
+} snerg_bake_field;
+
+/* Bytes of device workspace snerg_bake needs (G^3 flags, G^3 block list, counters); 0 if
+ * the description is invalid or G = N / B > 256. */
+size_t snerg_bake_workspace_bytes(const snerg_scene_desc* desc);
+
+/* Bake an analytic field into the Sec. 5.1 representation on the GPU (Sec. 5.3-5.4):
+ *   1. alpha = 1 - exp(-sigma v) at every voxel centre of the N^3 grid (v = extent / N);
+ *      a macroblock is kept iff its largest alpha is >= tau_alpha (the paper also culls by
+ *      visibility from the training views; there are no training views here);
+ *   2. kept macroblocks get atlas slots 0, 1, ... in raster order of the indirection grid
+ *      (x fastest), culled ones -1;
+ *   3. each voxel of a kept block stores the average of the field over its 16 jittered
+ *      positions (voxel centre + jitter * v), as 8-bit codes round(255 x) clamped to
+ *      [0, 255]: density as sigma / desc->sigma_max, then the 7 channels.
+ * Outputs (device, caller-owned): d_indirection int32 [G][G][G] (z, y, x); d_atlas uint8
+ * [max_blocks][B][B][B][8] laid out as snerg_create reads it. *num_blocks (host) receives
+ * the number of kept blocks. If that exceeds max_blocks the atlas is not written and
+ * SNERG_E_NOMEM is returned (retry with max_blocks = *num_blocks). desc->bg, max_steps and
+ * flags are not used. Floating point: FP32 with the library's expf / sinf; codes agree with
+ * an exact evaluation except where the exact value lies within about 1e-5 of a rounding
+ * boundary (and likewise for the tau_alpha decision). SYNCHRONISES `stream`. */
+snerg_status snerg_bake(const snerg_scene_desc* desc, const snerg_bake_field* field,
+                        int32_t* d_indirection, uint8_t* d_atlas, int64_t max_blocks,
+                        void* d_workspace, size_t ws_bytes, int64_t* num_blocks, void* stream);
+
 /* SYNCHRONISES `stream`, returns and clears the device status word (SNERG_OK or the
  * first device error recorded since the last call), or SNERG_E_CUDA if the stream
  * reports an asynchronous CUDA error. */

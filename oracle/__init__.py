@@ -62,6 +62,8 @@ def _lib():
         lib.oracle_ray.restype = ctypes.c_int
         lib.oracle_bake.argtypes = [i32, i32, P, f32, f32, f32, i32, P, P, P, P, P, i64, P]
         lib.oracle_bake.restype = ctypes.c_int64
+        lib.oracle_bake_blocks.argtypes = [i32, i32, P, f32, f32, i32, P, P, P, i64, P, P, P, P]
+        lib.oracle_bake_blocks.restype = None
         _LIB = lib
     return _LIB
 
@@ -225,3 +227,21 @@ def bake(N, B, bmin, extent, sigma_max, blobs, colors, jitter, tau_alpha=0.005, 
     if nb < 0:
         raise OracleError("more kept blocks than max_blocks")
     return ind, atlas[:nb].copy(), amax
+
+
+def bake_blocks(N, B, bmin, extent, sigma_max, blobs, colors, jitter, blocks):
+    """Maximum alpha and 8-bit content of the listed macroblocks (raster indices
+    b = x + G (y + G z)), kept or not: (alpha [n] f64, content [n,B,B,B,8] uint8,
+    raw [n,B,B,B,8] f64 = 255 x before rounding)."""
+    blobs = np.ascontiguousarray(blobs, np.float32).reshape(-1, 5)
+    colors = np.ascontiguousarray(colors, np.float32).reshape(7, 4)
+    jitter = np.ascontiguousarray(jitter, np.float32).reshape(16, 3)
+    blocks = np.ascontiguousarray(blocks, np.int64)
+    bmin = np.asarray(bmin, np.float32)
+    amax = np.zeros(blocks.shape[0], np.float64)
+    content = np.zeros((blocks.shape[0], B, B, B, 8), np.uint8)
+    raw = np.zeros((blocks.shape[0], B, B, B, 8), np.float64)
+    _lib().oracle_bake_blocks(int(N), int(B), _p(bmin), float(np.float32(extent)), float(np.float32(sigma_max)),
+                              blobs.shape[0], _p(blobs), _p(colors), _p(jitter), blocks.shape[0], _p(blocks),
+                              _p(amax), _p(content), _p(raw))
+    return amax, content, raw

@@ -573,6 +573,49 @@ static uint8_t quant8(double v) {
     return (uint8_t)floor(v * 255.0 + 0.5);
 }
 
+/* Largest alpha = 1 - exp(-sigma v) over the voxel centres of macroblock (bx, by, bz). */
+static double bake_block_alpha(int32_t B, const float* bmin, double v, int32_t n_blob, const float* blob,
+                               int32_t bx, int32_t by, int32_t bz) {
+    double amax = 0.0;
+    for (int32_t z = 0; z < B; ++z)
+        for (int32_t y = 0; y < B; ++y)
+            for (int32_t x = 0; x < B; ++x) {
+                double px = bmin[0] + ((bx * B + x) + 0.5) * v;
+                double py = bmin[1] + ((by * B + y) + 0.5) * v;
+                double pz = bmin[2] + ((bz * B + z) + 0.5) * v;
+                double a = -expm1(-field_sigma(blob, n_blob, px, py, pz) * v);
+                if (a > amax) amax = a;
+            }
+    return amax;
+}
+
+/* The 8 codes of every voxel of macroblock (bx, by, bz): the field averaged over the 16
+ * jittered positions (voxel centre + jitter * v), density divided by sigma_max. */
+static void bake_block_fill(int32_t B, const float* bmin, double v, float sigma_max, int32_t n_blob,
+                            const float* blob, const float* color, const float* jitter, int32_t bx, int32_t by,
+                            int32_t bz, uint8_t* out_block, double* raw_block /* nullable: 255 x before rounding */) {
+    for (int32_t z = 0; z < B; ++z)
+        for (int32_t y = 0; y < B; ++y)
+            for (int32_t x = 0; x < B; ++x) {
+                double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int sidx = 0; sidx < 16; ++sidx) {
+                    double px = bmin[0] + ((bx * B + x) + 0.5 + jitter[3 * sidx]) * v;
+                    double py = bmin[1] + ((by * B + y) + 0.5 + jitter[3 * sidx + 1]) * v;
+                    double pz = bmin[2] + ((bz * B + z) + 0.5 + jitter[3 * sidx + 2]) * v;
+                    acc[0] += field_sigma(blob, n_blob, px, py, pz);
+                    for (int c = 0; c < 7; ++c) acc[1 + c] += field_channel(color, c, px, py, pz);
+                }
+                const int64_t o = (((int64_t)z * B + y) * B + x) * 8;
+                uint8_t* out = out_block + o;
+                out[0] = quant8(acc[0] / 16.0 / (double)sigma_max);
+                for (int c = 0; c < 7; ++c) out[1 + c] = quant8(acc[1 + c] / 16.0);
+                if (raw_block) {
+                    raw_block[o] = acc[0] / 16.0 / (double)sigma_max * 255.0;
+                    for (int c = 0; c < 7; ++c) raw_block[o + 1 + c] = acc[1 + c] / 16.0 * 255.0;
+                }
+            }
+}
+
 /* Outputs: ind[G^3] (-1 or slot), atlas[max_blocks][B^3][8]; returns the number of
  * kept blocks (or -1 if more than max_blocks), and per-block maximum alpha in
  * block_alpha[G^3] (for diagnosing threshold ties). */
@@ -583,20 +626,9 @@ int64_t oracle_bake(int32_t N, int32_t B, const float* bmin, float extent, float
     const double v = (double)extent / (double)N;
     const int64_t G3 = (int64_t)G * G * G;
     #pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t b = 0; b < G3; ++b) {
-        int32_t bx = (int32_t)(b % G), by = (int32_t)((b / G) % G), bz = (int32_t)(b / ((int64_t)G * G));
-        double amax = 0.0;
-        for (int32_t z = 0; z < B; ++z)
-            for (int32_t y = 0; y < B; ++y)
-                for (int32_t x = 0; x < B; ++x) {
-                    double px = bmin[0] + ((bx * B + x) + 0.5) * v;
-                    double py = bmin[1] + ((by * B + y) + 0.5) * v;
-                    double pz = bmin[2] + ((bz * B + z) + 0.5) * v;
-                    double a = -expm1(-field_sigma(blob, n_blob, px, py, pz) * v);
-                    if (a > amax) amax = a;
-                }
-        block_alpha[b] = amax;
-    }
+    for (int64_t b = 0; b < G3; ++b)
+        block_alpha[b] = bake_block_alpha(B, bmin, v, n_blob, blob, (int32_t)(b % G), (int32_t)((b / G) % G),
+                                          (int32_t)(b / ((int64_t)G * G)));
     int64_t nb = 0;
     for (int64_t b = 0; b < G3; ++b) {
         if (block_alpha[b] >= (double)tau_alpha) {
@@ -610,22 +642,29 @@ int64_t oracle_bake(int32_t N, int32_t B, const float* bmin, float extent, float
     #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < G3; ++b) {
         if (ind[b] < 0) continue;
-        int32_t bx = (int32_t)(b % G), by = (int32_t)((b / G) % G), bz = (int32_t)(b / ((int64_t)G * G));
-        for (int32_t z = 0; z < B; ++z)
-            for (int32_t y = 0; y < B; ++y)
-                for (int32_t x = 0; x < B; ++x) {
-                    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    for (int sidx = 0; sidx < 16; ++sidx) {
-                        double px = bmin[0] + ((bx * B + x) + 0.5 + jitter[3 * sidx]) * v;
-                        double py = bmin[1] + ((by * B + y) + 0.5 + jitter[3 * sidx + 1]) * v;
-                        double pz = bmin[2] + ((bz * B + z) + 0.5 + jitter[3 * sidx + 2]) * v;
-                        acc[0] += field_sigma(blob, n_blob, px, py, pz);
-                        for (int c = 0; c < 7; ++c) acc[1 + c] += field_channel(color, c, px, py, pz);
-                    }
-                    uint8_t* out = atlas + ((int64_t)ind[b] * vox + ((int64_t)z * B + y) * B + x) * 8;
-                    out[0] = quant8(acc[0] / 16.0 / (double)sigma_max);
-                    for (int c = 0; c < 7; ++c) out[1 + c] = quant8(acc[1 + c] / 16.0);
-                }
+        bake_block_fill(B, bmin, v, sigma_max, n_blob, blob, color, jitter, (int32_t)(b % G),
+                        (int32_t)((b / G) % G), (int32_t)(b / ((int64_t)G * G)), atlas + (int64_t)ind[b] * vox * 8,
+                        NULL);
     }
     return nb;
+}
+
+/* The same quantities for a list of macroblocks (raster indices), whether kept or not:
+ * their maximum alpha and their 8-bit content, and optionally the values before rounding
+ * (255 x), which tell how close each code is to a rounding boundary. For sampled checks
+ * of large bakes. */
+void oracle_bake_blocks(int32_t N, int32_t B, const float* bmin, float extent, float sigma_max, int32_t n_blob,
+                        const float* blob, const float* color, const float* jitter, int64_t n,
+                        const int64_t* blocks, double* block_alpha, uint8_t* content, double* raw) {
+    const int32_t G = N / B;
+    const double v = (double)extent / (double)N;
+    const int64_t vox = (int64_t)B * B * B;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t b = blocks[i];
+        const int32_t bx = (int32_t)(b % G), by = (int32_t)((b / G) % G), bz = (int32_t)(b / ((int64_t)G * G));
+        block_alpha[i] = bake_block_alpha(B, bmin, v, n_blob, blob, bx, by, bz);
+        bake_block_fill(B, bmin, v, sigma_max, n_blob, blob, color, jitter, bx, by, bz, content + i * vox * 8,
+                        raw ? raw + i * vox * 8 : NULL);
+    }
 }

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsnerg.so")
-SOURCES = ["snerg_api.cu", "snerg_fwd.cu", "snerg_bwd.cu", "snerg_prep.cu", "snerg_noalloc.cu", "snerg_train.cu"]
+SOURCES = ["snerg_api.cu", "snerg_fwd.cu", "snerg_bwd.cu", "snerg_prep.cu", "snerg_noalloc.cu", "snerg_train.cu",
+           "snerg_bake.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

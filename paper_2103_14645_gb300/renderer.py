@@ -28,7 +28,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error"
 EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_render_rays",
             "snerg_render_backward", "snerg_last_status", "snerg_launch_count",
             "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc",
-            "snerg_set_mlp", "snerg_l2_loss", "snerg_adam_step"]
+            "snerg_set_mlp", "snerg_l2_loss", "snerg_adam_step", "snerg_bake_workspace_bytes", "snerg_bake"]
+MAX_BAKE_BLOBS = 64
 
 
 class SnergError(RuntimeError):
@@ -47,6 +48,12 @@ class RenderOpts(ctypes.Structure):
     _fields_ = [("d_aux", ctypes.c_void_p), ("d_counts", ctypes.c_void_p), ("d_trace", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_int32), ("persistent", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+class BakeField(ctypes.Structure):
+    _fields_ = [("n_blob", ctypes.c_int32), ("tau_alpha", ctypes.c_float),
+                ("blob", (ctypes.c_float * 5) * MAX_BAKE_BLOBS), ("color", (ctypes.c_float * 4) * 7),
+                ("jitter", (ctypes.c_float * 3) * 16)]
 
 
 _LIB = None
@@ -91,6 +98,10 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_set_mlp.restype = ctypes.c_int
     lib.snerg_render_rays_noalloc.argtypes = [P, P, P, i64, P, i32, P, i64, P, P, P, P]
     lib.snerg_render_rays_noalloc.restype = ctypes.c_int
+    lib.snerg_bake_workspace_bytes.argtypes = [P]
+    lib.snerg_bake_workspace_bytes.restype = ctypes.c_size_t
+    lib.snerg_bake.argtypes = [P, P, P, P, i64, P, ctypes.c_size_t, P, P]
+    lib.snerg_bake.restype = ctypes.c_int
     _LIB = lib
     return lib
 
@@ -361,3 +372,51 @@ class FineTuner:
         self.steps += 1
         adam_step(self.mlp, self.m, self.v, self.grad, self.steps, self.lr, self.betas, self.eps)
         return self.loss
+
+
+def bake_field(blobs, colors, jitter, tau_alpha: float = 0.005) -> BakeField:
+    """Pack an analytic field (blobs [n,5] = centre xyz, std, peak; colors [7,4] = w xyz,
+    phi; jitter [16,3] in voxel units) into the snerg_bake_field struct."""
+    blobs = np.asarray(blobs, np.float32).reshape(-1, 5)
+    if blobs.shape[0] > MAX_BAKE_BLOBS:
+        raise ValueError(f"at most {MAX_BAKE_BLOBS} blobs")
+    f = BakeField()
+    f.n_blob = blobs.shape[0]
+    f.tau_alpha = float(tau_alpha)
+    ctypes.memmove(f.blob, np.ascontiguousarray(blobs).ctypes.data, blobs.nbytes)
+    ctypes.memmove(f.color, np.ascontiguousarray(colors, np.float32).reshape(7, 4).ctypes.data, 7 * 4 * 4)
+    ctypes.memmove(f.jitter, np.ascontiguousarray(jitter, np.float32).reshape(16, 3).ctypes.data, 16 * 3 * 4)
+    return f
+
+
+def bake(N: int, B: int, bmin, extent: float, sigma_max: float, field: BakeField, device="cuda",
+         max_blocks: int | None = None):
+    """Bake an analytic field into (indirection int32 [G,G,G], atlas uint8 [nb,B,B,B,8]) on
+    the GPU with snerg_bake (Sec. 5.3-5.4). With max_blocks None the atlas is sized by a
+    first call that only counts the kept blocks."""
+    lib = load_library()
+    device = torch.device(device)
+    if device.type != "cuda":
+        raise ValueError("bake needs a CUDA device")
+    desc = SceneDesc(int(N), int(B), (ctypes.c_float * 3)(*bmin), float(extent), float(sigma_max),
+                     (ctypes.c_float * 3)(0, 0, 0), 0, 0)
+    nbytes = lib.snerg_bake_workspace_bytes(ctypes.byref(desc))
+    if nbytes == 0:
+        raise ValueError("invalid scene description for baking")
+    G = N // B
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    ind = torch.empty((G, G, G), dtype=torch.int32, device=device)
+    nb = ctypes.c_int64(0)
+    with torch.cuda.device(device):
+        st = _stream(device)
+        if max_blocks is None:
+            code = lib.snerg_bake(ctypes.byref(desc), ctypes.byref(field), _ptr(ind), None, 0, _ptr(ws), nbytes,
+                                  ctypes.byref(nb), st)
+            if code not in (0, 2):
+                _check(code, "snerg_bake")
+            max_blocks = nb.value
+        atlas = torch.empty((max_blocks, B, B, B, 8), dtype=torch.uint8, device=device)
+        code = lib.snerg_bake(ctypes.byref(desc), ctypes.byref(field), _ptr(ind), _ptr(atlas) if max_blocks else None,
+                              int(max_blocks), _ptr(ws), nbytes, ctypes.byref(nb), st)
+    _check(code, "snerg_bake")
+    return ind, atlas[:nb.value]

@@ -378,3 +378,25 @@ def custom_scene(N: int, B: int, ind: np.ndarray, atlas: np.ndarray, sigma_max: 
                  sigma_max=float(sigma_max), bg=tuple(bg), ind=np.ascontiguousarray(ind, np.int32),
                  atlas=np.ascontiguousarray(atlas, np.uint8), mlp=np.ascontiguousarray(mlp, np.float32),
                  cameras=np.ascontiguousarray(cameras), flags=int(flags))
+
+
+def analytic_field(seed: int, n_blob: int = 64, radius: float = 0.6, std=(0.03, 0.08), peak=(20.0, 200.0),
+                   freq: float = 8.0) -> dict:
+    """Seeded parameters of an analytic radiance field to bake (the stand-in for a trained
+    network): n_blob Gaussian density blobs with centres on a sphere of `radius` around the
+    origin (a surface-like, mostly empty scene), std and peak uniform in the given ranges
+    (world units); 7 sinusoidal channels (diffuse RGB, 4 features) with direction vectors
+    uniform in [-freq, freq]^3 and phases in [0, 2 pi); 16 jitter offsets drawn from a
+    Gaussian of std 1/sqrt(12) voxels (the anti-aliasing samples of the bake)."""
+    rng = np.random.default_rng(seed)
+    u = rng.normal(size=(n_blob, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    blobs = np.zeros((n_blob, 5), np.float32)
+    blobs[:, :3] = radius * u
+    blobs[:, 3] = rng.uniform(*std, n_blob)
+    blobs[:, 4] = rng.uniform(*peak, n_blob)
+    colors = np.zeros((7, 4), np.float32)
+    colors[:, :3] = rng.uniform(-freq, freq, (7, 3))
+    colors[:, 3] = rng.uniform(0.0, 2.0 * np.pi, 7)
+    jitter = (rng.normal(size=(16, 3)) / np.sqrt(12.0)).astype(np.float32)
+    return {"blobs": blobs, "colors": colors, "jitter": jitter}

@@ -112,3 +112,43 @@ def test_no_cpu_fallback_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(renderer, "_LIB", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         renderer.load_library(str(tmp_path / "missing.so"))
+
+
+def test_bake_workspace_and_invalid_arguments(lib):
+    """snerg_bake sizes its workspace as G^3 flags + G^3 slot list + a header line, refuses
+    grids with G > 256, and rejects bad fields and pointers before any CUDA call."""
+    for N, B in [(64, 8), (1024, 32), (16, 2), (2048, 8)]:
+        G = N // B
+        got = lib.snerg_bake_workspace_bytes(ctypes.byref(_desc(N, B)))
+        assert 8 * G ** 3 + 256 <= got <= 8 * G ** 3 + 3 * 256 and got % 256 == 0
+    for bad in [_desc(4096, 8), _desc(64, 6), _desc(64, 8, sigma=0.0), _desc(64, 8, extent=-1.0)]:
+        assert lib.snerg_bake_workspace_bytes(ctypes.byref(bad)) == 0
+    assert lib.snerg_bake_workspace_bytes(None) == 0
+    f = synth.analytic_field(0, n_blob=8)
+    field = renderer.bake_field(f["blobs"], f["colors"], f["jitter"])
+    assert ctypes.sizeof(field) == 8 + 64 * 20 + 7 * 16 + 16 * 12
+    d = _desc()
+    nb = ctypes.c_int64(-1)
+    ws = lib.snerg_bake_workspace_bytes(ctypes.byref(d))
+
+    def call(fld, ind=256, atlas=256, maxb=10, wsp=256, wsb=ws, out=ctypes.byref(nb)):
+        return lib.snerg_bake(ctypes.byref(d), ctypes.byref(fld) if fld is not None else None, ind, atlas, maxb,
+                              wsp, wsb, out, None)
+
+    assert call(None) == 1
+    assert call(field, ind=None) == 1
+    assert call(field, out=None) == 1
+    assert call(field, maxb=-1) == 1
+    assert call(field, atlas=None) == 1
+    assert call(field, atlas=260) == 1          # atlas not 8-byte aligned
+    assert call(field, wsp=None) == 1
+    assert call(field, wsp=264) == 1            # workspace not 256-byte aligned
+    assert call(field, wsb=ws - 1) == 2
+    for mutate in [lambda g: setattr(g, "n_blob", 65), lambda g: setattr(g, "n_blob", -1),
+                   lambda g: setattr(g, "tau_alpha", 0.0), lambda g: setattr(g, "tau_alpha", 1.0),
+                   lambda g: g.blob[0].__setitem__(3, 0.0), lambda g: g.blob[1].__setitem__(4, -1.0),
+                   lambda g: g.blob[2].__setitem__(0, float("inf")), lambda g: g.color[3].__setitem__(1, float("nan")),
+                   lambda g: g.jitter[5].__setitem__(2, 8.5)]:
+        g = renderer.bake_field(f["blobs"], f["colors"], f["jitter"])
+        mutate(g)
+        assert call(g) == 1

@@ -158,3 +158,26 @@ def test_bake_max_blocks_overflow_raises():
     with pytest.raises(oracle.OracleError):
         oracle.bake(8, 4, (-1, -1, -1), 2.0, 40.0, _flat_blob(30.0), _still_colors(np.zeros(7)),
                     np.zeros((16, 3), np.float32), max_blocks=3)
+
+
+def test_bake_blocks_agrees_with_whole_bake():
+    """The per-block entry (used for sampled checks of large bakes) returns the whole
+    bake's block maxima and, for kept blocks, its atlas content; its raw values round to
+    the stored codes."""
+    N, B = 32, 8
+    rng = np.random.default_rng(5)
+    blobs = np.zeros((6, 5), np.float32)
+    blobs[:, :3] = rng.uniform(-0.6, 0.6, (6, 3))
+    blobs[:, 3] = rng.uniform(0.05, 0.2, 6)
+    blobs[:, 4] = rng.uniform(5, 40, 6)
+    colors = np.zeros((7, 4), np.float32)
+    colors[:, :3] = rng.uniform(-6, 6, (7, 3))
+    colors[:, 3] = rng.uniform(0, 6.28, 7)
+    jit = (rng.normal(size=(16, 3)) / math.sqrt(12)).astype(np.float32)
+    ind, atl, amax = oracle.bake(N, B, (-1, -1, -1), 2.0, 50.0, blobs, colors, jit)
+    blocks = np.arange((N // B) ** 3)
+    a2, content, raw = oracle.bake_blocks(N, B, (-1, -1, -1), 2.0, 50.0, blobs, colors, jit, blocks)
+    np.testing.assert_array_equal(a2, amax.ravel())
+    kept = ind.ravel() >= 0
+    np.testing.assert_array_equal(content[kept], atl[ind.ravel()[kept]])
+    np.testing.assert_array_equal(content, _quant(raw / 255.0))
