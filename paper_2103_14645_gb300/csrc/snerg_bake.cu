@@ -4,15 +4,18 @@
 // averaged over 16 Gaussian-jittered positions) stored as 8-bit codes.
 //
 // Three launches and one read-back:
-//   alpha pass   one CTA per work item (256 voxels of one macroblock, block-major), flags
-//                the macroblock if any of its voxel centres has alpha >= tau_alpha;
+//   alpha pass   persistent CTAs walk the macroblocks; each evaluates its block 256 voxel
+//                centres at a time and stops at the first chunk holding alpha >= tau_alpha;
 //   scan         one CTA of 1024 threads numbers the flagged blocks (exclusive scan in
 //                raster order) into the indirection grid and a slot -> block list;
 //   fill pass    persistent CTAs walk the kept voxels (slot-major, so the atlas stores of
 //                a warp are one contiguous 256-byte run) and write 8 codes per voxel.
-// Every work item first keeps only the density blobs that can reach its voxels: a blob
-// whose exponent |x - c|^2 / (2 s^2) exceeds 120 over the item's box (jitter included)
-// has exp(-120) < 1e-52, which is 0 in binary32, so dropping it changes no result.
+// Each unit of work (a block in the alpha pass, 256 voxels in the fill pass) first keeps
+// only the density blobs that can matter over its box (jitter included): blob i is dropped
+// where peak_i exp(-|x - c_i|^2 / (2 s_i^2)) < eps over the whole box, with
+// eps = 2^-30 min(sigma_max, sigma_tau) and sigma_tau = -ln(1 - tau_alpha) / v the density
+// at which alpha reaches tau_alpha. The dropped terms change sigma by less than
+// 64 eps = 6e-8 of both the code step and the culling density.
 // The colour channels use angle addition: the mean over the 16 samples of
 // sin(a + b_s) with a = w . x_centre + phi and b_s = w . j_s v equals
 // sin a * mean(cos b_s) + cos a * mean(sin b_s), and the two means depend only on the
@@ -30,7 +33,6 @@ namespace bake_gpu {
 constexpr int kMaxBlobs = SNERG_BAKE_MAX_BLOBS;
 constexpr int kThreads = 256;
 constexpr int kScanThreads = 1024;
-constexpr float kCullExponent = 120.0f;
 constexpr int kMaxG = 256;
 constexpr size_t kAlign = 256;
 
@@ -43,7 +45,8 @@ struct BakeParams {
     float v, tau, inv_sigma_max;
     float bmin[3];
     float jit_lo[3], jit_hi[3]; // per-axis extremes of the jitter offsets (voxel units)
-    float blob[kMaxBlobs][5];   // centre xyz, k = 1 / (2 s^2), peak
+    float blob[kMaxBlobs][5];   // centre xyz, k = log2(e) / (2 s^2), peak
+    float cull[kMaxBlobs];      // ln(peak / eps) / ln 2: the blob is dropped beyond this k |x - c|^2
     float color[7][4];          // w xyz, phi
     float cbar[7], sbar[7];     // mean over the samples of cos / sin (w_c . j_s v)
     float jitter[16][3];
@@ -93,7 +96,7 @@ __device__ __forceinline__ int gather_blobs(const BakeParams& P, const ItemBox& 
             const float d = fmaxf(fmaxf(lo - c, c - hi), 0.0f);
             a = fmaf(d, d, a);
         }
-        rel = a * P.blob[t][3] <= kCullExponent;
+        rel = a * P.blob[t][3] <= P.cull[t];
     }
     int pos = 0;
     if (t < 64) {
@@ -118,7 +121,7 @@ __device__ __forceinline__ float density_at(const float4* s_blob, const float* s
         const float4 b = s_blob[i];
         const float dx = x - b.x, dy = y - b.y, dz = z - b.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        acc = fmaf(s_peak[i], expf(-d2 * b.w), acc);
+        acc = fmaf(s_peak[i], exp2f(-d2 * b.w), acc);
     }
     return acc;
 }
@@ -129,30 +132,39 @@ __device__ __forceinline__ uint32_t code8(float x) {
 }
 
 __global__ void __launch_bounds__(kThreads) bake_alpha_kernel(const __grid_constant__ BakeParams P,
-                                                              int32_t* __restrict__ flags, int64_t n_items) {
+                                                              int32_t* __restrict__ flags, int64_t G3) {
     __shared__ float4 s_blob[kMaxBlobs];
     __shared__ float s_peak[kMaxBlobs];
     __shared__ int s_cnt[2];
-    __shared__ int s_done;
-    const int t = threadIdx.x;
-    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int64_t b = it >> P.lg_items;
-        const int l0 = (int)(it & ((1 << P.lg_items) - 1)) * P.item_voxels;
+    const int t = threadIdx.x, m = P.B - 1;
+    const int n_chunks = 1 << P.lg_items;
+    for (int64_t b = blockIdx.x; b < G3; b += gridDim.x) {
         const int bx = (int)(b % P.G), by = (int)((b / P.G) % P.G), bz = (int)(b / ((int64_t)P.G * P.G));
-        __syncthreads();                                   // the previous item's readers are done
-        if (t == 0) s_done = flags[b];                     // an earlier item already kept the block
-        const int n = gather_blobs(P, item_box(P, bx, by, bz, l0), false, s_blob, s_peak, s_cnt);
-        if (n == 0 || s_done) continue;                    // uniform: alpha = 0 < tau, or nothing to add
-        bool keep = false;
-        if (t < P.item_voxels) {
-            const int l = l0 + t, m = P.B - 1;
-            const float x = P.bmin[0] + ((float)(bx * P.B + (l & m)) + 0.5f) * P.v;
-            const float y = P.bmin[1] + ((float)(by * P.B + ((l >> P.lgB) & m)) + 0.5f) * P.v;
-            const float z = P.bmin[2] + ((float)(bz * P.B + (l >> (2 * P.lgB))) + 0.5f) * P.v;
-            const float sigma = density_at(s_blob, s_peak, n, x, y, z);
-            keep = -expm1f(-sigma * P.v) >= P.tau;       // alpha = 1 - exp(-sigma v)
+        ItemBox box;
+        box.lo[0] = bx * P.B;
+        box.lo[1] = by * P.B;
+        box.lo[2] = bz * P.B;
+        box.hi[0] = box.lo[0] + m;
+        box.hi[1] = box.lo[1] + m;
+        box.hi[2] = box.lo[2] + m;
+        __syncthreads();                                   // the previous block's readers are done
+        const int n = gather_blobs(P, box, false, s_blob, s_peak, s_cnt);
+        if (n == 0) continue;                              // uniform: alpha = 0 < tau everywhere
+        for (int ch = 0; ch < n_chunks; ++ch) {
+            bool keep = false;
+            if (t < P.item_voxels) {
+                const int l = ch * P.item_voxels + t;
+                const float x = P.bmin[0] + ((float)(box.lo[0] + (l & m)) + 0.5f) * P.v;
+                const float y = P.bmin[1] + ((float)(box.lo[1] + ((l >> P.lgB) & m)) + 0.5f) * P.v;
+                const float z = P.bmin[2] + ((float)(box.lo[2] + (l >> (2 * P.lgB))) + 0.5f) * P.v;
+                const float sigma = density_at(s_blob, s_peak, n, x, y, z);
+                keep = -expm1f(-sigma * P.v) >= P.tau;   // alpha = 1 - exp(-sigma v)
+            }
+            if (__syncthreads_or(keep)) {
+                if (t == 0) flags[b] = 1;
+                break;                                     // uniform
+            }
         }
-        if (__syncthreads_or(keep) && t == 0) flags[b] = 1;
     }
 }
 
@@ -349,11 +361,14 @@ extern "C" snerg_status snerg_bake(const snerg_scene_desc* desc, const snerg_bak
         P.jit_lo[k] = lo;
         P.jit_hi[k] = hi;
     }
+    const double sigma_tau = -std::log1p(-(double)field->tau_alpha) / v;
+    const double eps = std::ldexp(std::fmin((double)desc->sigma_max, sigma_tau), -30);
     for (int i = 0; i < field->n_blob; ++i) {
         for (int k = 0; k < 3; ++k) P.blob[i][k] = field->blob[i][k];
-        const double s = field->blob[i][3];
-        P.blob[i][3] = (float)(1.0 / (2.0 * s * s));
-        P.blob[i][4] = field->blob[i][4];
+        const double s = field->blob[i][3], peak = field->blob[i][4];
+        P.blob[i][3] = (float)(1.0 / (2.0 * s * s * std::log(2.0)));
+        P.blob[i][4] = (float)peak;
+        P.cull[i] = peak > eps ? (float)(std::log(peak / eps) / std::log(2.0)) : -1.0f;
     }
     std::memcpy(P.color, field->color, sizeof(P.color));
     std::memcpy(P.jitter, field->jitter, sizeof(P.jitter));
@@ -375,10 +390,9 @@ extern "C" snerg_status snerg_bake(const snerg_scene_desc* desc, const snerg_bak
     int64_t* d_count = (int64_t*)(ws + L.count);
     int32_t* d_flags = (int32_t*)(ws + L.flags);
     int32_t* d_list = (int32_t*)(ws + L.list);
-    const int64_t n_items = G3 << P.lg_items;
     cudaError_t e = cudaMemsetAsync(d_flags, 0, (size_t)G3 * 4, st);
     if (e == cudaSuccess) {
-        bake_alpha_kernel<<<grid_for((const void*)bake_alpha_kernel, n_items), kThreads, 0, st>>>(P, d_flags, n_items);
+        bake_alpha_kernel<<<grid_for((const void*)bake_alpha_kernel, G3), kThreads, 0, st>>>(P, d_flags, G3);
         bake_scan_kernel<<<1, kScanThreads, 0, st>>>(d_flags, G3, d_indirection, d_list, d_count);
         e = cudaGetLastError();
     }

@@ -9,6 +9,8 @@ boundary. Error budget of the kernel's value before rounding, in code units (255
            2e-5 relative; band 5e-5 * raw + 1e-3;
   colour:  sin of an argument |w . x + phi| <= 8 * 5 + 2 pi accurate to a few ulp of 47
            (4e-6 each), halved, times 255: below 2e-3; band 4e-3.
+Blobs left out where their term is below 2^-30 min(sigma_max, sigma_tau) move the
+density by less than 64 * 2^-30 * 255 = 1.5e-5 code units, inside the density band.
 Outside the band the codes are equal; inside it they differ by at most 1. The tau_alpha
 decision is exact outside |alpha_max - tau| <= 5e-5 tau."""
 import numpy as np
