@@ -38,9 +38,13 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "render_image_shell1024.md")
 CSRC = os.path.join(ROOT, "paper_2103_14645_gb300", "csrc")
 
 
+# the sources the forward render kernels are compiled from (march core + launchers)
+RENDER_SOURCES = ("snerg_internal.cuh", "snerg_fwd.cu")
+
+
 def kernel_source_digest() -> str:
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
+    for f in RENDER_SOURCES:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
