@@ -252,7 +252,7 @@ size_t snerg_bake_workspace_bytes(const snerg_scene_desc* desc);
  * [max_blocks][B][B][B][8] laid out as snerg_create reads it. *num_blocks (host) receives
  * the number of kept blocks. If that exceeds max_blocks the atlas is not written and
  * SNERG_E_NOMEM is returned (retry with max_blocks = *num_blocks). desc->bg, max_steps and
- * flags are not used. Floating point: binary32 (exp2f, sincosf); over each unit of work a
+ * flags are not used. Floating point: binary32 (PTX ex2.approx, sincosf); over each unit of work a
  * blob is left out where its term stays below 2^-30 min(sigma_max, sigma_tau), sigma_tau =
  * -ln(1 - tau_alpha) / v. Codes agree with an exact evaluation except where the exact value
  * lies within about 1e-5 of a rounding boundary (and likewise for the tau_alpha decision).

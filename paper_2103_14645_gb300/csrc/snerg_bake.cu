@@ -49,7 +49,8 @@ struct BakeParams {
     float cull[kMaxBlobs];      // ln(peak / eps) / ln 2: the blob is dropped beyond this k |x - c|^2
     float color[7][4];          // w xyz, phi
     float cbar[7], sbar[7];     // mean over the samples of cos / sin (w_c . j_s v)
-    float jitter[16][3];
+    float jv[16][3];            // jitter offsets times v (world units)
+    float jq[16];               // |jv_s|^2
 };
 
 struct ItemBox {
@@ -114,6 +115,14 @@ __device__ __forceinline__ int gather_blobs(const BakeParams& P, const ItemBox& 
     return s_cnt[0] + s_cnt[1];
 }
 
+// 2^x with the PTX approximate base-2 exponential (relative error about 2^-22 over the
+// exponents used here, which are >= -cull > -64).
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float density_at(const float4* s_blob, const float* s_peak, int n, float x, float y,
                                             float z) {
     float acc = 0.0f;
@@ -121,7 +130,7 @@ __device__ __forceinline__ float density_at(const float4* s_blob, const float* s
         const float4 b = s_blob[i];
         const float dx = x - b.x, dy = y - b.y, dz = z - b.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        acc = fmaf(s_peak[i], exp2f(-d2 * b.w), acc);
+        acc = fmaf(s_peak[i], ex2(-d2 * b.w), acc);
     }
     return acc;
 }
@@ -234,17 +243,21 @@ __global__ void __launch_bounds__(kThreads) bake_fill_kernel(const __grid_consta
         const float fx = (float)(bx * P.B + (l & m)) + 0.5f;
         const float fy = (float)(by * P.B + ((l >> P.lgB) & m)) + 0.5f;
         const float fz = (float)(bz * P.B + (l >> (2 * P.lgB))) + 0.5f;
-        float sigma = 0.0f;
-        if (n > 0) {
-#pragma unroll 1
-            for (int s = 0; s < 16; ++s) {
-                const float x = P.bmin[0] + (fx + P.jitter[s][0]) * P.v;
-                const float y = P.bmin[1] + (fy + P.jitter[s][1]) * P.v;
-                const float z = P.bmin[2] + (fz + P.jitter[s][2]) * P.v;
-                sigma += density_at(s_blob, s_peak, n, x, y, z);
-            }
-        }
         const float cx = P.bmin[0] + fx * P.v, cy = P.bmin[1] + fy * P.v, cz = P.bmin[2] + fz * P.v;
+        // sum over blobs of peak * sum over samples of 2^(-k |D + jv_s|^2), D = centre - c,
+        // expanded as -k |D|^2 - 2k D . jv_s - k |jv_s|^2: four FMAs per blob and sample
+        float sigma = 0.0f;
+        for (int i = 0; i < n; ++i) {
+            const float4 b = s_blob[i];
+            const float dx = cx - b.x, dy = cy - b.y, dz = cz - b.z;
+            const float a = -b.w * fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float gx = -2.0f * b.w * dx, gy = -2.0f * b.w * dy, gz = -2.0f * b.w * dz;
+            float part = 0.0f;
+#pragma unroll
+            for (int s = 0; s < 16; ++s)
+                part += ex2(fmaf(gx, P.jv[s][0], fmaf(gy, P.jv[s][1], fmaf(gz, P.jv[s][2], fmaf(-b.w, P.jq[s], a)))));
+            sigma = fmaf(s_peak[i], part, sigma);
+        }
         uint32_t q[8];
         q[0] = code8(sigma * 0.0625f * P.inv_sigma_max);
 #pragma unroll
@@ -371,7 +384,15 @@ extern "C" snerg_status snerg_bake(const snerg_scene_desc* desc, const snerg_bak
         P.cull[i] = peak > eps ? (float)(std::log(peak / eps) / std::log(2.0)) : -1.0f;
     }
     std::memcpy(P.color, field->color, sizeof(P.color));
-    std::memcpy(P.jitter, field->jitter, sizeof(P.jitter));
+    for (int j = 0; j < 16; ++j) {
+        double q = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double o = (double)field->jitter[j][k] * v;
+            P.jv[j][k] = (float)o;
+            q += o * o;
+        }
+        P.jq[j] = (float)q;
+    }
     for (int c = 0; c < 7; ++c) {
         double cs = 0.0, sn = 0.0;
         for (int s = 0; s < 16; ++s) {

@@ -1,12 +1,14 @@
 """GPU bake (snerg_bake, Sec. 5.3-5.4) against the FP64 oracle bake.
 
-The kernel evaluates the field in binary32 (expf, sincosf), the oracle in FP64, so a code
-can differ only where the exact value lies within the kernel's error of a rounding
-boundary. Error budget of the kernel's value before rounding, in code units (255 x):
-  density: each blob term exp(-|x - c|^2 k) carries the rounding of x (|x| <= 2, 2^-23
-           relative) amplified by the exponent's slope 2 |x - c| k <= 2 * 3 s / (2 s^2)
-           (about 100 for s = 0.03) plus a few ulp of expf and of the sums, i.e. below
-           2e-5 relative; band 5e-5 * raw + 1e-3;
+The kernel evaluates the field in binary32 (the PTX base-2 exponential ex2.approx,
+sincosf), the oracle in FP64, so a code can differ only where the exact value lies within
+the kernel's error of a rounding boundary. Error budget of the kernel's value before
+rounding, in code units (255 x):
+  density: each blob term 2^(-k |x - c|^2) (k in base-2 units) carries the rounding of x
+           (|x| <= 2, 2^-23 relative) amplified by the exponent's slope 2 |x - c| k
+           (about 100 for s = 0.03), the rounding of the expanded exponent (a few ulp of
+           |exponent| <= 40, i.e. <= 1e-5 absolute), about 2^-22 relative of ex2.approx and
+           a few ulp of the sums: below 2e-5 relative; band 5e-5 * raw + 1e-3;
   colour:  sin of an argument |w . x + phi| <= 8 * 5 + 2 pi accurate to a few ulp of 47
            (4e-6 each), halved, times 255: below 2e-3; band 4e-3.
 Blobs left out where their term is below 2^-30 min(sigma_max, sigma_tau) move the
