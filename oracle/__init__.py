@@ -64,6 +64,8 @@ def _lib():
         lib.oracle_bake.restype = ctypes.c_int64
         lib.oracle_bake_blocks.argtypes = [i32, i32, P, f32, f32, i32, P, P, P, i64, P, P, P, P]
         lib.oracle_bake_blocks.restype = None
+        lib.oracle_requantize.argtypes = [P, i64, P]
+        lib.oracle_requantize.restype = None
         _LIB = lib
     return _LIB
 
@@ -192,21 +194,57 @@ def adam_step(param, m, v, grad, step, lr=3e-4, betas=(0.9, 0.999), eps=1e-8):
     return param
 
 
-def finetune_steps(scene, pix, target, mlp, steps, lr=3e-4):
+def requantize(x) -> np.ndarray:
+    """8-bit codes of float32 values (Sec. 5.4): floor(255 x + 1/2) clamped, decided in
+    binary32."""
+    x = np.ascontiguousarray(x, np.float32)
+    out = np.zeros(x.shape, np.uint8)
+    _lib().oracle_requantize(_p(x), x.size, _p(out))
+    return out
+
+
+def finetune_steps(scene, pix, target, mlp, steps, lr=3e-4, atlas_lr=None):
     """`steps` fine-tuning steps of the MLP with the oracle's render and adjoint and the
-    reference Adam; returns (the parameter after each step, the loss before each step)."""
+    reference Adam; returns (the parameter after each step, the loss before each step).
+
+    With atlas_lr, the colour and feature values are fine-tuned too: an FP64 shadow copy
+    of the decoded atlas (initialised from binary32 q / 255) takes Adam steps on the
+    adjoint's atlas gradient, and after each step channels 1..7 of the atlas are
+    requantised from it (density codes stay frozen). The render of the next step reads
+    the requantised codes. Then the third return value is the codes after each step."""
     w = np.asarray(mlp, np.float64).copy()
     m = np.zeros_like(w)
     v = np.zeros_like(w)
-    params, losses = [], []
+    codes = np.ascontiguousarray(scene.atlas, np.uint8).copy()
+    sc = scene
+    if atlas_lr is not None:
+        shadow = (codes.astype(np.float32) / np.float32(255.0)).astype(np.float64)
+        ma = np.zeros_like(shadow)
+        va = np.zeros_like(shadow)
+    params, losses, history = [], [], []
     for t in range(1, steps + 1):
-        out = render_rays(scene, pix, mlp=w)
+        out = render_rays(sc, pix, mlp=w)
         d = out["rgb"] - np.asarray(target, np.float64)
         losses.append(float((d * d).sum()))
-        _, g = backward_rays(scene, pix, 2.0 * d, mlp=w, atlas_grad=False)
+        ga, g = backward_rays(sc, pix, 2.0 * d, mlp=w, atlas_grad=atlas_lr is not None)
         adam_step(w, m, v, g, t, lr)
         params.append(w.copy())
+        if atlas_lr is not None:
+            adam_step(shadow, ma, va, ga, t, atlas_lr)
+            codes = codes.copy()
+            codes[..., 1:] = requantize(shadow[..., 1:])
+            sc = _with_atlas(scene, codes)
+            history.append(codes)
+    if atlas_lr is not None:
+        return params, losses, history
     return params, losses
+
+
+def _with_atlas(scene, codes):
+    import copy
+    sc = copy.copy(scene)
+    sc.atlas = codes
+    return sc
 
 
 def bake(N, B, bmin, extent, sigma_max, blobs, colors, jitter, tau_alpha=0.005, max_blocks=None):

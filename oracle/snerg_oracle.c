@@ -668,3 +668,15 @@ void oracle_bake_blocks(int32_t N, int32_t B, const float* bmin, float extent, f
                         raw ? raw + i * vox * 8 : NULL);
     }
 }
+
+
+/* ------------------------------------------------------------------------- */
+/* 8-bit requantisation (Sec. 5.4) of fine-tuned values: code = floor(255 x + 1/2) clamped
+ * to [0, 255], the rounding decision taken in binary32 (one fused multiply-add, correctly
+ * rounded, then floor), the precision the kernels decide it in. NaN -> 0. */
+void oracle_requantize(const float* x, int64_t n, uint8_t* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        const float q = floorf(fmaf(x[i], 255.0f, 0.5f));
+        out[i] = q > 0.0f ? (q < 255.0f ? (uint8_t)q : 255) : 0;
+    }
+}
