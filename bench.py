@@ -396,6 +396,14 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
     out["finetune"] = {"ms_per_step": round(float(np.mean(ms_ft)), 4),
                        "mrays_s": round(n / (np.mean(ms_ft) * 1e-3) / 1e6, 3),
                        "steps_per_s": round(1e3 / float(np.mean(ms_ft)), 1)}
+    # the same steps also fine-tuning the baked colours/features through an FP32 shadow
+    # atlas, requantised into the scene's codes after every step
+    rs = renderer.Renderer.from_scene(wsc, dev)
+    fta = renderer.FineTuner(rs, wsc.mlp, atlas=wsc.atlas, atlas_lr=1.0 / 255.0)
+    ms_fa = time_steps(lambda: fta.step(wsc.cameras, pix, tgt), reps, 2, stream, flush)
+    out["finetune"]["shadow_atlas_ms_per_step"] = round(float(np.mean(ms_fa)), 4)
+    out["finetune"]["shadow_atlas_values"] = int(fta.shadow.numel())
+    del rs, fta
     del rb, ga, gm
     out["bake"] = bake_section(args, dev, stream, flush)
     if not args.no_large:

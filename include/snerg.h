@@ -175,6 +175,23 @@ snerg_status snerg_render_backward(snerg_handle h, const snerg_camera* cams, int
                                    const int32_t* d_fwd_counts, float* d_grad_atlas,
                                    float* d_grad_mlp, void* stream);
 
+/* Requantise fine-tuned colour and feature values into the scene. The paper fine-tunes the
+ * view-dependence MLP against the training images (Sec. 5.5); the baked colours and
+ * features can be fine-tuned the same way through an FP32 shadow copy that takes the
+ * optimiser's steps on the d_grad_atlas of snerg_render_backward, and this call turns the
+ * shadow back into the 8-bit codes the renderer reads (Sec. 5.4).
+ *   d_values    : float32 [num_blocks][B][B][B][8] (16-byte aligned), the atlas layout;
+ *                 channels 1..7 (diffuse RGB, features) are read as values x and stored as
+ *                 floor(255 x + 1/2) clamped to [0, 255], decided in binary32 (NaN -> 0);
+ *                 channel 0 is ignored: densities stay frozen, and with them the
+ *                 empty-space maps built by snerg_create.
+ *   d_atlas_out : nullable uint8 [num_blocks][B][B][B][8] (8-byte aligned); receives the
+ *                 new codes with the scene's density codes in channel 0.
+ * Rewrites every stored voxel of the handle's padded atlas and its copies in the
+ * neighbouring blocks' aprons. Asynchronous on `stream`; later calls on the same stream
+ * render the new codes. */
+snerg_status snerg_requantize_atlas(snerg_handle h, const float* d_values, uint8_t* d_atlas_out, void* stream);
+
 /* Photometric loss of Eq. 3 over n rays: *d_loss += sum |C - C*|^2 (ACCUMULATED, caller
  * zeroes; nullable), d_grad [n][3] = 2 (C - C*) (nullable). d_rgb, d_target: [n][3]. */
 snerg_status snerg_l2_loss(const float* d_rgb, const float* d_target, int64_t n, float* d_grad,

@@ -205,6 +205,27 @@ extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t
     return SNERG_OK;
 }
 
+namespace snerg {
+// snerg_prep.cu
+cudaError_t launch_requantize_padded(const int32_t* ind, const int32_t* blk_of_slot, const float* values, int64_t nb,
+                                     int N, int B, int lgB, uint2* patlas, uint8_t* atlas_out, cudaStream_t st);
+}  // namespace snerg
+
+extern "C" snerg_status snerg_requantize_atlas(snerg_handle h, const float* d_values, uint8_t* d_atlas_out,
+                                             void* stream) {
+    if (!h) return SNERG_E_INVAL;
+    if (h->nb == 0) return SNERG_OK;
+    if (!d_values || ((uintptr_t)d_values & 15u) || ((uintptr_t)d_atlas_out & 7u)) return SNERG_E_INVAL;
+    Layout L;
+    make_layout(&h->desc, h->nb, &L);
+    const cudaError_t e = launch_requantize_padded(h->ds.ind, (const int32_t*)(h->ws + L.blk), d_values, h->nb,
+                                                   h->ds.N, h->ds.B, h->ds.lgB, (uint2*)(h->ws + L.patlas), d_atlas_out,
+                                                   (cudaStream_t)stream);
+    if (e != cudaSuccess) return SNERG_E_CUDA;
+    ++h->launches;
+    return SNERG_OK;
+}
+
 static bool opts_debug(const snerg_render_opts* o) {
     return o && (o->d_aux || o->d_counts || (o->d_trace && o->trace_cap > 0));
 }

@@ -54,6 +54,45 @@ __global__ void build_padded_kernel(const int32_t* __restrict__ ind, const int32
     }
 }
 
+// Requantisation of fine-tuned colour/feature values into the padded atlas (Sec. 5.4
+// codes): every padded entry whose source voxel is stored takes channels 1..7 from
+// floor(255 x + 1/2) of the source's values (binary32, clamped) and keeps its own density
+// byte, so the empty-space maps built from the densities stay valid. Interior entries
+// also go to atlas_out (nullable) in the unpadded layout.
+__device__ __forceinline__ uint32_t quant8(float x) {
+    const float q = floorf(__fmaf_rn(x, 255.0f, 0.5f));
+    return q > 0.0f ? (q < 255.0f ? (uint32_t)q : 255u) : 0u;   // NaN -> 0
+}
+
+__global__ void requantize_padded_kernel(const int32_t* __restrict__ ind, const int32_t* __restrict__ blk_of_slot,
+                                         const float4* __restrict__ values, int64_t nb, int N, int B, int lgB,
+                                         uint2* __restrict__ patlas, uint2* __restrict__ atlas_out) {
+    const int P = B + 2, P3 = P * P * P, G = N >> lgB;
+    const int64_t total = nb * (int64_t)P3, B3 = (int64_t)B * B * B;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = t / P3;
+        const int r = (int)(t - slot * P3);
+        const int px = r % P, py = (r / P) % P, pz = r / (P * P);
+        const int blk = blk_of_slot[slot];
+        if (blk < 0) continue;
+        const int bx = blk % G, by = (blk / G) % G, bz = blk / (G * G);
+        const int gx = min(max(bx * B + px - 1, 0), N - 1);
+        const int gy = min(max(by * B + py - 1, 0), N - 1);
+        const int gz = min(max(bz * B + pz - 1, 0), N - 1);
+        const int owner = ind[((gz >> lgB) * G + (gy >> lgB)) * G + (gx >> lgB)];
+        if (owner < 0) continue;                               // apron of an empty block: stays 0
+        const int loc = ((gz & (B - 1)) * B + (gy & (B - 1))) * B + (gx & (B - 1));
+        const int64_t src = (int64_t)owner * B3 + loc;
+        const float4 a = values[2 * src], b = values[2 * src + 1];
+        const uint2 old = patlas[t];
+        uint2 v;
+        v.x = (old.x & 0xffu) | quant8(a.y) << 8 | quant8(a.z) << 16 | quant8(a.w) << 24;
+        v.y = quant8(b.x) | quant8(b.y) << 8 | quant8(b.z) << 16 | quant8(b.w) << 24;
+        patlas[t] = v;
+        if (atlas_out && px >= 1 && px <= B && py >= 1 && py <= B && pz >= 1 && pz <= B) atlas_out[src] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------------
 // Chebyshev (L-infinity) distance transform of cubes of side n, in three separable
 // passes: along one axis, out(p) = min over q on p's line of max(|q - p|, in(q)),
@@ -197,6 +236,16 @@ cudaError_t launch_build_padded(const int32_t* ind, const int32_t* blk_of_slot, 
     const int64_t total = nb * (int64_t)(B + 2) * (B + 2) * (B + 2);
     build_padded_kernel<<<grid_for(total), 256, 0, st>>>(ind, blk_of_slot, reinterpret_cast<const uint2*>(atlas), nb,
                                                           N, B, lgB, patlas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_requantize_padded(const int32_t* ind, const int32_t* blk_of_slot, const float* values, int64_t nb,
+                                     int N, int B, int lgB, uint2* patlas, uint8_t* atlas_out, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    const int64_t total = nb * (int64_t)(B + 2) * (B + 2) * (B + 2);
+    requantize_padded_kernel<<<grid_for(total), 256, 0, st>>>(ind, blk_of_slot, reinterpret_cast<const float4*>(values),
+                                                               nb, N, B, lgB, patlas,
+                                                               reinterpret_cast<uint2*>(atlas_out));
     return cudaGetLastError();
 }
 

@@ -28,7 +28,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error"
 EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_render_rays",
             "snerg_render_backward", "snerg_last_status", "snerg_launch_count",
             "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc",
-            "snerg_set_mlp", "snerg_l2_loss", "snerg_adam_step", "snerg_bake_workspace_bytes", "snerg_bake"]
+            "snerg_set_mlp", "snerg_l2_loss", "snerg_adam_step", "snerg_bake_workspace_bytes", "snerg_bake",
+            "snerg_requantize_atlas"]
 MAX_BAKE_BLOBS = 64
 
 
@@ -98,6 +99,8 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_set_mlp.restype = ctypes.c_int
     lib.snerg_render_rays_noalloc.argtypes = [P, P, P, i64, P, i32, P, i64, P, P, P, P]
     lib.snerg_render_rays_noalloc.restype = ctypes.c_int
+    lib.snerg_requantize_atlas.argtypes = [P, P, P, P]
+    lib.snerg_requantize_atlas.restype = ctypes.c_int
     lib.snerg_bake_workspace_bytes.argtypes = [P]
     lib.snerg_bake_workspace_bytes.restype = ctypes.c_size_t
     lib.snerg_bake.argtypes = [P, P, P, P, i64, P, ctypes.c_size_t, P, P]
@@ -197,6 +200,20 @@ class Renderer:
     def check_status(self):
         """Synchronise and raise if a kernel recorded a device-side error."""
         _check(self.lib.snerg_last_status(self.handle, _stream(self.device)), "device status")
+
+    def requantize_atlas(self, values: torch.Tensor, atlas_out: torch.Tensor | None = None):
+        """Write fine-tuned colour/feature values (float32 [nb,B,B,B,8], channel 0 ignored)
+        into the scene as 8-bit codes (snerg_requantize_atlas); optionally also into
+        atlas_out (uint8, same shape, density codes in channel 0)."""
+        _require_cuda(values, "values", torch.float32)
+        if tuple(values.shape) != (self.nb, self.B, self.B, self.B, 8):
+            raise ValueError("values must have the atlas shape [nb, B, B, B, 8]")
+        if atlas_out is not None:
+            _require_cuda(atlas_out, "atlas_out", torch.uint8)
+            if atlas_out.shape != values.shape:
+                raise ValueError("atlas_out must have the atlas shape")
+        _check(self.lib.snerg_requantize_atlas(self.handle, _ptr(values), _ptr(atlas_out), _stream(self.device)),
+               "snerg_requantize_atlas")
 
     def _opts(self, n_pix, aux, counts, trace_cap, persistent, tile, ctas_per_sm):
         out = {}
@@ -348,9 +365,15 @@ class FineTuner:
     """Fine-tunes the view-dependence MLP of a baked grid against observed pixels with
     Adam and the L2 loss, as the paper does after baking (Sec. 5.5: Adam, learning rate
     3e-4). One step = render_rays (keeping per-ray state) -> loss and dL/dC -> backward
-    (dL/dPhi) -> Adam, all in the library's kernels."""
+    (dL/dPhi) -> Adam, all in the library's kernels.
 
-    def __init__(self, renderer: Renderer, mlp, lr: float = 3e-4, betas=(0.9, 0.999), eps: float = 1e-8):
+    With `atlas` (the scene's uint8 atlas [nb,B,B,B,8]) and `atlas_lr`, the baked colours
+    and features are fine-tuned too: an FP32 shadow copy (q / 255) takes Adam steps on the
+    backward's atlas gradient (zero on the density channel, which stays frozen) and is
+    requantised into the scene's 8-bit codes after every step."""
+
+    def __init__(self, renderer: Renderer, mlp, lr: float = 3e-4, betas=(0.9, 0.999), eps: float = 1e-8,
+                 atlas=None, atlas_lr: float | None = None):
         self.r = renderer
         self.mlp = torch.as_tensor(np.asarray(mlp, np.float32)).to(renderer.device).contiguous()
         self.m = torch.zeros_like(self.mlp)
@@ -359,6 +382,17 @@ class FineTuner:
         self.loss = torch.zeros(1, dtype=torch.float32, device=renderer.device)
         self.lr, self.betas, self.eps = lr, betas, eps
         self.steps = 0
+        self.atlas_lr = atlas_lr
+        self.shadow = None
+        if atlas_lr is not None:
+            if atlas is None:
+                raise ValueError("atlas_lr needs the scene's atlas")
+            codes = torch.as_tensor(np.asarray(atlas, np.uint8)).to(renderer.device)
+            self.shadow = (codes.float() / 255.0).contiguous()
+            self.ma = torch.zeros_like(self.shadow)
+            self.va = torch.zeros_like(self.shadow)
+            self.grad_atlas = torch.zeros_like(self.shadow)
+            self.codes = torch.empty_like(codes)
 
     def step(self, cams, pix: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
         """One Adam step on rays pix [n,3] with observed colours target [n,3]; returns the
@@ -368,9 +402,16 @@ class FineTuner:
         self.loss.zero_()
         self.grad.zero_()
         l2_loss(fwd["rgb"], target, g, self.loss)
-        self.r.backward(cams, pix, self.mlp, g, None, self.grad, fwd_aux=fwd["aux"], fwd_counts=fwd["counts"])
+        ga = None
+        if self.shadow is not None:
+            self.grad_atlas.zero_()
+            ga = self.grad_atlas
+        self.r.backward(cams, pix, self.mlp, g, ga, self.grad, fwd_aux=fwd["aux"], fwd_counts=fwd["counts"])
         self.steps += 1
         adam_step(self.mlp, self.m, self.v, self.grad, self.steps, self.lr, self.betas, self.eps)
+        if self.shadow is not None:
+            adam_step(self.shadow, self.ma, self.va, self.grad_atlas, self.steps, self.atlas_lr, self.betas, self.eps)
+            self.r.requantize_atlas(self.shadow, self.codes)
         return self.loss
 
 
