@@ -89,6 +89,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.snerg_render_rays(None, cams.ctypes.data, 1, None, 0, None, None, None, None) == 1
     assert lib.snerg_render_backward(None, cams.ctypes.data, 1, None, 0, None, None, None, None, None, None, None) == 1
     assert lib.snerg_last_status(None, None) == 1
+    assert lib.snerg_requantize_atlas(None, 256, None, None) == 1
     assert lib.snerg_launch_count(None) == 0
     lib.snerg_destroy(None)
 
