@@ -60,9 +60,9 @@ def _lib():
         lib.oracle_mlp_input.restype = None
         lib.oracle_ray.argtypes = [i32, f32, P, P, i32, i32, P]
         lib.oracle_ray.restype = ctypes.c_int
-        lib.oracle_bake.argtypes = [i32, i32, P, f32, f32, f32, i32, P, P, P, P, P, i64, P]
+        lib.oracle_bake.argtypes = [i32, i32, P, f32, f32, f32, i32, P, P, P, P, P, i64, P, i32]
         lib.oracle_bake.restype = ctypes.c_int64
-        lib.oracle_bake_blocks.argtypes = [i32, i32, P, f32, f32, i32, P, P, P, i64, P, P, P, P]
+        lib.oracle_bake_blocks.argtypes = [i32, i32, P, f32, f32, i32, P, P, P, i64, P, P, P, P, i32]
         lib.oracle_bake_blocks.restype = None
         lib.oracle_requantize.argtypes = [P, i64, P]
         lib.oracle_requantize.restype = None
@@ -247,9 +247,11 @@ def _with_atlas(scene, codes):
     return sc
 
 
-def bake(N, B, bmin, extent, sigma_max, blobs, colors, jitter, tau_alpha=0.005, max_blocks=None):
+def bake(N, B, bmin, extent, sigma_max, blobs, colors, jitter, tau_alpha=0.005, max_blocks=None,
+         alpha_codes=False):
     """FP64 bake of the analytic field (Sec. 5.3): returns (ind [G,G,G] int32,
-    atlas [nb,B,B,B,8] uint8, block max alpha [G,G,G] f64)."""
+    atlas [nb,B,B,B,8] uint8, block max alpha [G,G,G] f64). With alpha_codes, channel 0
+    stores alpha = 1 - exp(-sigma v) of the averaged density instead of sigma / sigma_max."""
     G = N // B
     blobs = np.ascontiguousarray(blobs, np.float32).reshape(-1, 5)
     colors = np.ascontiguousarray(colors, np.float32).reshape(7, 4)
@@ -261,13 +263,13 @@ def bake(N, B, bmin, extent, sigma_max, blobs, colors, jitter, tau_alpha=0.005, 
     amax = np.zeros((G, G, G), np.float64)
     nb = _lib().oracle_bake(int(N), int(B), _p(bmin), float(np.float32(extent)), float(np.float32(sigma_max)),
                             float(np.float32(tau_alpha)), blobs.shape[0], _p(blobs), _p(colors), _p(jitter),
-                            _p(ind), _p(atlas), int(max_blocks), _p(amax))
+                            _p(ind), _p(atlas), int(max_blocks), _p(amax), int(bool(alpha_codes)))
     if nb < 0:
         raise OracleError("more kept blocks than max_blocks")
     return ind, atlas[:nb].copy(), amax
 
 
-def bake_blocks(N, B, bmin, extent, sigma_max, blobs, colors, jitter, blocks):
+def bake_blocks(N, B, bmin, extent, sigma_max, blobs, colors, jitter, blocks, alpha_codes=False):
     """Maximum alpha and 8-bit content of the listed macroblocks (raster indices
     b = x + G (y + G z)), kept or not: (alpha [n] f64, content [n,B,B,B,8] uint8,
     raw [n,B,B,B,8] f64 = 255 x before rounding)."""
@@ -281,5 +283,5 @@ def bake_blocks(N, B, bmin, extent, sigma_max, blobs, colors, jitter, blocks):
     raw = np.zeros((blocks.shape[0], B, B, B, 8), np.float64)
     _lib().oracle_bake_blocks(int(N), int(B), _p(bmin), float(np.float32(extent)), float(np.float32(sigma_max)),
                               blobs.shape[0], _p(blobs), _p(colors), _p(jitter), blocks.shape[0], _p(blocks),
-                              _p(amax), _p(content), _p(raw))
+                              _p(amax), _p(content), _p(raw), int(bool(alpha_codes)))
     return amax, content, raw

@@ -25,6 +25,9 @@
  *   * optional partial un-premultiply (App. C, forward-facing scenes): after compositing,
  *     (C_d, alpha, V) *= min(1, 1.5 alpha) / alpha where alpha = 1 - T_final > 0, so the
  *     MLP sees the scaled C_d and V and the background weight becomes 1 - min(1, 1.5 alpha);
+ *   * optional alpha atlas (App. A keeps alpha in its own texture): channel 0 holds alpha
+ *     codes, the sample's alpha is the trilinear code / 255, T <- T (1 - alpha), and the
+ *     exit test is T < 1e-3 on a binary32 running product;
  *   * the backward pass is the exact adjoint of the above w.r.t. the decoded colour and
  *     feature values and the MLP weights, with density frozen (Sec. 5.5 fine-tunes the
  *     per-pixel network against an L2 image loss, Eq. 3);
@@ -85,6 +88,9 @@ typedef struct {
     int64_t max_iter;
     int unpremultiply;     /* App. C partial un-premultiply */
     int per_sample_mlp;    /* non-deferred comparison model */
+    int alpha_atlas;       /* channel 0 holds alpha codes (App. A's alpha texture) */
+    float tmin32;          /* binary32(1e-3): the alpha-atlas exit threshold on T */
+    float inv255_32;       /* binary32(1 / 255) */
     const double* mlp;     /* weights, for the per-sample model */
 } OScene;
 
@@ -189,6 +195,7 @@ static void march(const OScene* S, const ORay* r, uint64_t* trace, int32_t trace
     const int32_t N = S->N;
     const int64_t vox = (int64_t)S->B * S->B * S->B;
     float tau = 0.0f;
+    float Tc = 1.0f;        /* alpha atlas: binary32 transmittance of the exit test */
     for (int64_t k = 0;; ++k) {
         if (k >= S->max_iter) { out->status = OR_E_STEP_LIMIT; return; }
         float tk = r->t_start + ((float)k + 0.5f);
@@ -240,8 +247,18 @@ static void march(const OScene* S, const ORay* r, uint64_t* trace, int32_t trace
         float e0 = e00 * g32[1] + e10 * f32[1];
         float e1 = e01 * g32[1] + e11 * f32[1];
         float s32 = e0 * g32[2] + e1 * f32[2];
-        float od32 = s32 * S->kappa32;
-        tau = tau + od32;
+        int saturated;
+        if (S->alpha_atlas) {
+            /* channel 0 is alpha itself: a = s * binary32(1/255), T <- T (1 - a), stop once
+             * T < binary32(1e-3) */
+            float a32 = s32 * S->inv255_32;
+            Tc = Tc * (1.0f - a32);
+            saturated = Tc < S->tmin32;
+        } else {
+            float od32 = s32 * S->kappa32;
+            tau = tau + od32;
+            saturated = tau > S->taumax32;
+        }
 
         /* FP64 compositing, Eqs. 2, 5, 6 */
         double qi = 0.0;
@@ -250,7 +267,7 @@ static void march(const OScene* S, const ORay* r, uint64_t* trace, int32_t trace
                 for (int c = 0; c < 2; ++c) qi += w64[a][b][c] * (double)q[a][b][c];
         double sigma = qi / 255.0 * S->sigma_max;
         double x = sigma * S->delta;
-        double alpha = -expm1(-x);
+        double alpha = S->alpha_atlas ? qi / 255.0 : -expm1(-x);
         double wk = out->T * alpha;
         if (S->per_sample_mlp) {
             double cdk[3] = {0, 0, 0}, vk[4] = {0, 0, 0, 0}, x[34];
@@ -284,8 +301,8 @@ static void march(const OScene* S, const ORay* r, uint64_t* trace, int32_t trace
                     for (int ch = 0; ch < 3; ++ch) out->cd[ch] += cw * channel_value(S, X, Y, Z, 1 + ch);
                     for (int ch = 0; ch < 4; ++ch) out->v[ch] += cw * channel_value(S, X, Y, Z, 4 + ch);
                 }
-        out->T *= exp(-x);
-        if (tau > S->taumax32) break;                  /* opacity saturated */
+        out->T *= S->alpha_atlas ? 1.0 - alpha : exp(-x);
+        if (saturated) break;                          /* opacity saturated */
     }
 }
 
@@ -397,9 +414,12 @@ static int scene_init(OScene* S, int32_t N, int32_t B, const float* bmin, float 
     S->kappa32 = (float)(sigma_max * ((double)extent / (double)N) / 255.0);
     S->taumax32 = (float)log(1000.0);
     S->max_iter = 4 * (int64_t)N + 16;
-    if ((flags & ~3) || (flags & 3) == 3) return OR_E_INVAL;   /* un-premultiply is a deferred-model option */
+    if ((flags & ~7) || (flags & 3) == 3) return OR_E_INVAL;   /* un-premultiply is a deferred-model option */
     S->unpremultiply = (flags & 1) != 0;
     S->per_sample_mlp = (flags & 2) != 0;
+    S->alpha_atlas = (flags & 4) != 0;
+    S->tmin32 = (float)1e-3;
+    S->inv255_32 = (float)(1.0 / 255.0);
     S->mlp = NULL;
     for (int64_t i = 0; i < (int64_t)S->G * S->G * S->G; ++i)
         if (ind[i] < -1 || ind[i] >= nb) return OR_E_INVAL;
@@ -593,7 +613,8 @@ static double bake_block_alpha(int32_t B, const float* bmin, double v, int32_t n
  * jittered positions (voxel centre + jitter * v), density divided by sigma_max. */
 static void bake_block_fill(int32_t B, const float* bmin, double v, float sigma_max, int32_t n_blob,
                             const float* blob, const float* color, const float* jitter, int32_t bx, int32_t by,
-                            int32_t bz, uint8_t* out_block, double* raw_block /* nullable: 255 x before rounding */) {
+                            int32_t bz, uint8_t* out_block, double* raw_block /* nullable: 255 x before rounding */,
+                            int32_t alpha_codes /* channel 0 = 1 - exp(-sigma v) instead of sigma / sigma_max */) {
     for (int32_t z = 0; z < B; ++z)
         for (int32_t y = 0; y < B; ++y)
             for (int32_t x = 0; x < B; ++x) {
@@ -607,10 +628,11 @@ static void bake_block_fill(int32_t B, const float* bmin, double v, float sigma_
                 }
                 const int64_t o = (((int64_t)z * B + y) * B + x) * 8;
                 uint8_t* out = out_block + o;
-                out[0] = quant8(acc[0] / 16.0 / (double)sigma_max);
+                const double d0 = alpha_codes ? -expm1(-acc[0] / 16.0 * v) : acc[0] / 16.0 / (double)sigma_max;
+                out[0] = quant8(d0);
                 for (int c = 0; c < 7; ++c) out[1 + c] = quant8(acc[1 + c] / 16.0);
                 if (raw_block) {
-                    raw_block[o] = acc[0] / 16.0 / (double)sigma_max * 255.0;
+                    raw_block[o] = d0 * 255.0;
                     for (int c = 0; c < 7; ++c) raw_block[o + 1 + c] = acc[1 + c] / 16.0 * 255.0;
                 }
             }
@@ -621,7 +643,7 @@ static void bake_block_fill(int32_t B, const float* bmin, double v, float sigma_
  * block_alpha[G^3] (for diagnosing threshold ties). */
 int64_t oracle_bake(int32_t N, int32_t B, const float* bmin, float extent, float sigma_max, float tau_alpha,
                     int32_t n_blob, const float* blob, const float* color, const float* jitter /*[16][3]*/,
-                    int32_t* ind, uint8_t* atlas, int64_t max_blocks, double* block_alpha) {
+                    int32_t* ind, uint8_t* atlas, int64_t max_blocks, double* block_alpha, int32_t alpha_codes) {
     const int32_t G = N / B;
     const double v = (double)extent / (double)N;
     const int64_t G3 = (int64_t)G * G * G;
@@ -644,7 +666,7 @@ int64_t oracle_bake(int32_t N, int32_t B, const float* bmin, float extent, float
         if (ind[b] < 0) continue;
         bake_block_fill(B, bmin, v, sigma_max, n_blob, blob, color, jitter, (int32_t)(b % G),
                         (int32_t)((b / G) % G), (int32_t)(b / ((int64_t)G * G)), atlas + (int64_t)ind[b] * vox * 8,
-                        NULL);
+                        NULL, alpha_codes);
     }
     return nb;
 }
@@ -655,7 +677,8 @@ int64_t oracle_bake(int32_t N, int32_t B, const float* bmin, float extent, float
  * of large bakes. */
 void oracle_bake_blocks(int32_t N, int32_t B, const float* bmin, float extent, float sigma_max, int32_t n_blob,
                         const float* blob, const float* color, const float* jitter, int64_t n,
-                        const int64_t* blocks, double* block_alpha, uint8_t* content, double* raw) {
+                        const int64_t* blocks, double* block_alpha, uint8_t* content, double* raw,
+                        int32_t alpha_codes) {
     const int32_t G = N / B;
     const double v = (double)extent / (double)N;
     const int64_t vox = (int64_t)B * B * B;
@@ -665,7 +688,7 @@ void oracle_bake_blocks(int32_t N, int32_t B, const float* bmin, float extent, f
         const int32_t bx = (int32_t)(b % G), by = (int32_t)((b / G) % G), bz = (int32_t)(b / ((int64_t)G * G));
         block_alpha[i] = bake_block_alpha(B, bmin, v, n_blob, blob, bx, by, bz);
         bake_block_fill(B, bmin, v, sigma_max, n_blob, blob, color, jitter, bx, by, bz, content + i * vox * 8,
-                        raw ? raw + i * vox * 8 : NULL);
+                        raw ? raw + i * vox * 8 : NULL, alpha_codes);
     }
 }
 

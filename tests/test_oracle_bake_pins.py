@@ -181,3 +181,20 @@ def test_bake_blocks_agrees_with_whole_bake():
     kept = ind.ravel() >= 0
     np.testing.assert_array_equal(content[kept], atl[ind.ravel()[kept]])
     np.testing.assert_array_equal(content, _quant(raw / 255.0))
+
+
+def test_bake_alpha_codes_closed_form():
+    """With alpha codes, a constant density sigma stores round(255 (1 - exp(-sigma v))) in
+    channel 0 (the viewer's alpha texture, App. A); the culling and the other channels are
+    unchanged."""
+    N, B, extent = 16, 4, 2.0
+    v = extent / N
+    jit = np.random.default_rng(3).normal(size=(16, 3)).astype(np.float32) / math.sqrt(12)
+    args = (N, B, (-1, -1, -1), extent, 40.0, _flat_blob(3.0), _still_colors(np.full(7, 0.7)), jit)
+    ind_s, atl_s, _ = oracle.bake(*args)
+    ind_a, atl_a, _ = oracle.bake(*args, alpha_codes=True)
+    want = int(math.floor(255.0 * -math.expm1(-3.0 * v) + 0.5))
+    assert want == 80
+    assert (atl_a[..., 0] == want).all()
+    np.testing.assert_array_equal(ind_a, ind_s)
+    np.testing.assert_array_equal(atl_a[..., 1:], atl_s[..., 1:])

@@ -202,10 +202,11 @@ def test_mlp_input_layout():
     np.testing.assert_allclose(x, np.concatenate(ref), rtol=0, atol=1e-15)
 
 
-def _brute_force_ray(scene, dense, mlp, cam, px, py, unpremultiply=False):
+def _brute_force_ray(scene, dense, mlp, cam, px, py, unpremultiply=False, alpha_atlas=False):
     """Definition of the march evaluated by library routines on a dense grid:
     trilinear by scipy.ndimage.map_coordinates (order 1, clamp-to-edge), transmittance
-    by a running product, MLP by torch float64 linear layers."""
+    by a running product, MLP by torch float64 linear layers. With alpha_atlas, channel 0
+    is alpha: a = trilinear / 255, T <- T (1 - a), stop once T < 1e-3."""
     from scipy.ndimage import map_coordinates
     N, B = scene.N, scene.B
     hit, o, d, ts, te = oracle.ray(scene, cam, px, py)
@@ -232,12 +233,13 @@ def _brute_force_ray(scene, dense, mlp, cam, px, py, unpremultiply=False):
         coord = (np.asarray(u[::-1], np.float64) - 0.5).reshape(3, 1)
         s = map_coordinates(dens, coord, order=1, mode="nearest")[0]
         sd = s / 255.0 * sigma_max * delta
-        w = T * (1 - math.exp(-sd))
+        a = s / 255.0 if alpha_atlas else 1 - math.exp(-sd)
+        w = T * a
         for c in range(7):
             feat[c] += w * map_coordinates(chans[c], coord, order=1, mode="nearest")[0]
-        T *= math.exp(-sd)
+        T *= 1 - a if alpha_atlas else math.exp(-sd)
         tau += sd
-        if tau > math.log(1000.0):
+        if (T < 1e-3) if alpha_atlas else (tau > math.log(1000.0)):
             break
     raw = feat.copy()
     if unpremultiply and 1 - T > 0:
@@ -255,10 +257,12 @@ def _brute_force_ray(scene, dense, mlp, cam, px, py, unpremultiply=False):
     return rgb, raw, steps, visited
 
 
-@pytest.mark.parametrize("name,unpremultiply", [("tiny", False), ("gauss64", False), ("gauss64", True)])
-def test_brute_force_dense_grid(name, unpremultiply):
+@pytest.mark.parametrize("name,unpremultiply,alpha", [("tiny", False, False), ("gauss64", False, False),
+                                                       ("gauss64", True, False), ("tiny", False, True),
+                                                       ("gauss64", False, True), ("gauss64", True, True)])
+def test_brute_force_dense_grid(name, unpremultiply, alpha):
     sc = synth.make_scene(name)
-    sc.flags = 1 if unpremultiply else 0
+    sc.flags = (1 if unpremultiply else 0) | (4 if alpha else 0)
     dense = helpers.blocks_to_dense(sc)
     rng = np.random.default_rng(5)
     W, H = int(sc.cameras[0]["W"]), int(sc.cameras[0]["H"])
@@ -266,7 +270,7 @@ def test_brute_force_dense_grid(name, unpremultiply):
     out = oracle.render_rays(sc, pix, trace_cap=256)
     n_active_rays = 0
     for i, (c, x, y) in enumerate(pix):
-        rgb, feat, steps, visited = _brute_force_ray(sc, dense, sc.mlp, sc.cameras[c], x, y, unpremultiply)
+        rgb, feat, steps, visited = _brute_force_ray(sc, dense, sc.mlp, sc.cameras[c], x, y, unpremultiply, alpha)
         np.testing.assert_allclose(out["rgb"][i], rgb, rtol=0, atol=1e-10)
         np.testing.assert_allclose(out["aux"][i, :7], feat, rtol=0, atol=1e-10)
         assert out["counts"][i, 0] == steps
@@ -557,3 +561,66 @@ def test_per_sample_brute_force():
             if tau > math.log(1000.0):
                 break
         np.testing.assert_allclose(out["rgb"][i], rgb + T * np.asarray(sc.bg), rtol=0, atol=1e-10)
+
+
+# --------------------------------------------------------------------------------------
+# alpha atlas (App. A keeps alpha in its own texture): channel 0 = alpha codes
+# --------------------------------------------------------------------------------------
+
+def test_alpha_atlas_slab_closed_form():
+    """Uniform slab of alpha code q: every sample has alpha = q / 255, so after n samples
+    T = (1 - alpha)^n and C_d = c (1 - T); the march stops after the first sample with
+    T < 1e-3 (n = 10 for q = 128: 0.498^9 = 1.9e-3, 0.498^10 = 9.5e-4)."""
+    col = np.array([100, 150, 200, 10, 20, 30, 40])
+    sc = helpers.slab_scene(z_range=(2, 14), q=128, color=col, sigma_max_vox=1.0)
+    sc.flags = 4
+    out = oracle.render_rays(sc, np.array([[0, 0, 0]]), trace_cap=16)
+    a = 128 / 255.0
+    n = 10
+    assert (1 - a) ** (n - 1) >= 1e-3 > (1 - a) ** n
+    assert out["counts"][0, 1] == n
+    assert out["counts"][0, 0] == 2 + n      # 2 samples of block row z 12..15 before the slab
+    T = (1 - a) ** n
+    np.testing.assert_allclose(out["aux"][0, :3], col[:3] / 255.0 * (1 - T), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(out["aux"][0, 7], 1 - T, rtol=0, atol=1e-14)
+
+
+def test_alpha_atlas_equals_density_atlas_at_matched_alpha():
+    """A density code q_s with sigma_max chosen so that 1 - exp(-q_s/255 sigma_max delta)
+    equals q_a / 255 composites like the alpha code q_a: same counts, and the same colours
+    up to the binary32 rounding of sigma_max in the scene description (~1e-8)."""
+    col = np.array([90, 30, 220, 40, 50, 60, 70])
+    qa, qs = 77, 200
+    a = qa / 255.0
+    smax_vox = -math.log1p(-a) * 255.0 / qs
+    dens = helpers.slab_scene(z_range=(3, 12), q=qs, color=col, sigma_max_vox=smax_vox)
+    alph = helpers.slab_scene(z_range=(3, 12), q=qa, color=col, sigma_max_vox=smax_vox)
+    alph.flags = 4
+    pix = np.array([[0, 0, 0]])
+    o1 = oracle.render_rays(dens, pix)
+    o2 = oracle.render_rays(alph, pix)
+    np.testing.assert_allclose(o2["rgb"], o1["rgb"], rtol=0, atol=1e-7)
+    np.testing.assert_allclose(o2["aux"], o1["aux"], rtol=0, atol=1e-7)
+    np.testing.assert_array_equal(o2["counts"], o1["counts"])
+    assert o1["counts"][0, 1] == 9
+
+
+def test_alpha_atlas_gradient_matches_central_differences():
+    sc = synth.make_scene("tiny")
+    sc.flags = 4
+    pix = _pix(sc)[::2]
+    rng = np.random.default_rng(12)
+    target = rng.uniform(size=(pix.shape[0], 3))
+    val = sc.atlas.astype(np.float64) / 255.0
+    g_val, g_mlp = oracle.backward_rays(sc, pix, oracle.render_rays(sc, pix, val=val)["rgb"] - target, val=val)
+    occupied = np.argwhere(np.abs(g_val[..., 1:]) > 1e-3)
+    assert occupied.shape[0] > 10
+    h = 1e-6
+    for idx in occupied[rng.choice(occupied.shape[0], 8, replace=False)]:
+        i = tuple(idx[:-1]) + (idx[-1] + 1,)
+        vp, vm = val.copy(), val.copy()
+        vp[i] += h
+        vm[i] -= h
+        fp = _loss(sc, pix, target, val=vp)[0]
+        fm = _loss(sc, pix, target, val=vm)[0]
+        np.testing.assert_allclose(g_val[i], (fp - fm) / (2 * h), rtol=1e-5, atol=1e-8)
