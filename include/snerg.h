@@ -77,6 +77,14 @@ typedef struct {
  * residual. Forward only, one-camera launches only (snerg_render without persistent;
  * other entry points return SNERG_E_UNSUPPORTED); not combinable with UNPREMULTIPLY. */
 #define SNERG_FLAG_PER_SAMPLE_MLP 2
+/* Alpha atlas (App. A keeps alpha in its own 8-bit texture): channel 0 of the atlas holds
+ * alpha codes instead of density codes. A sample's alpha is a = s * binary32(1/255), s the
+ * binary32 trilinear of the codes (the same arithmetic as the density path), composited as
+ * w = T a, T <- T (1 - a) with the product rounded in binary32, and the ray stops after the
+ * sample that brings T below binary32(1e-3); sigma_max is not used. The empty-space maps,
+ * the probe (code 0 = empty) and all entry points but snerg_render_rays_noalloc work
+ * unchanged. snerg_bake with this flag stores alpha = 1 - exp(-sigma v) in channel 0. */
+#define SNERG_FLAG_ALPHA_ATLAS 4
 
 /* Pinhole camera (Sec. 4.1 r(t) = o + t d). 80 bytes, host memory.
  * Pixel (x, y) looks along R (x + 0.5 - cx) / fx, -(y + 0.5 - cy) / fy, -1) normalised,
@@ -268,8 +276,9 @@ size_t snerg_bake_workspace_bytes(const snerg_scene_desc* desc);
  * Outputs (device, caller-owned): d_indirection int32 [G][G][G] (z, y, x); d_atlas uint8
  * [max_blocks][B][B][B][8] laid out as snerg_create reads it. *num_blocks (host) receives
  * the number of kept blocks. If that exceeds max_blocks the atlas is not written and
- * SNERG_E_NOMEM is returned (retry with max_blocks = *num_blocks). desc->bg, max_steps and
- * flags are not used. Floating point: binary32 (PTX ex2.approx, sincosf); over each unit of work a
+ * SNERG_E_NOMEM is returned (retry with max_blocks = *num_blocks). desc->bg and max_steps
+ * are not used; of desc->flags only SNERG_FLAG_ALPHA_ATLAS matters (channel 0 then stores
+ * alpha = 1 - exp(-sigma v) of the averaged density). Floating point: binary32 (PTX ex2.approx, sincosf); over each unit of work a
  * blob is left out where its term stays below 2^-30 min(sigma_max, sigma_tau), sigma_tau =
  * -ln(1 - tau_alpha) / v. Codes agree with an exact evaluation except where the exact value
  * lies within about 1e-5 of a rounding boundary (and likewise for the tau_alpha decision).

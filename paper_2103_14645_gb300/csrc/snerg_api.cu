@@ -48,7 +48,7 @@ bool desc_ok(const snerg_scene_desc* d) {
     if (!(std::isfinite(d->extent) && d->extent > 0.0f)) return false;
     if (!(std::isfinite(d->sigma_max) && d->sigma_max >= 0.0f)) return false;
     if (d->max_steps < 0) return false;
-    if (d->flags & ~(SNERG_FLAG_UNPREMULTIPLY | SNERG_FLAG_PER_SAMPLE_MLP)) return false;
+    if (d->flags & ~(SNERG_FLAG_UNPREMULTIPLY | SNERG_FLAG_PER_SAMPLE_MLP | SNERG_FLAG_ALPHA_ATLAS)) return false;
     if ((d->flags & SNERG_FLAG_UNPREMULTIPLY) && (d->flags & SNERG_FLAG_PER_SAMPLE_MLP)) return false;
     return finite3(d->bmin) && finite3(d->bg);
 }
@@ -194,6 +194,8 @@ extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t
     }
     s.kappa = (float)((double)desc->sigma_max * ((double)desc->extent / (double)N) / 255.0);
     s.taumax = (float)std::log(1000.0);
+    s.tmin = (float)1e-3;
+    s.inv255 = (float)(1.0 / 255.0);
     s.kmax = desc->max_steps > 0 ? std::min(desc->max_steps, 4 * N + 16) : 4 * N + 16;
     s.flags = desc->flags;
 

@@ -41,7 +41,7 @@ struct BakeParams {
     int32_t n_blob;
     int32_t item_voxels;        // min(256, B^3)
     int32_t lg_items;           // log2(B^3 / item_voxels)
-    int32_t pad;
+    int32_t alpha_codes;        // channel 0 = 1 - exp(-sigma v) instead of sigma / sigma_max
     float v, tau, inv_sigma_max;
     float bmin[3];
     float jit_lo[3], jit_hi[3]; // per-axis extremes of the jitter offsets (voxel units)
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) bake_fill_kernel(const __grid_consta
             sigma = fmaf(s_peak[i], part, sigma);
         }
         uint32_t q[8];
-        q[0] = code8(sigma * 0.0625f * P.inv_sigma_max);
+        q[0] = P.alpha_codes ? code8(-expm1f(-sigma * 0.0625f * P.v)) : code8(sigma * 0.0625f * P.inv_sigma_max);
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
             const float a = fmaf(P.color[c][0], cx, fmaf(P.color[c][1], cy, fmaf(P.color[c][2], cz, P.color[c][3])));
@@ -359,6 +359,7 @@ extern "C" snerg_status snerg_bake(const snerg_scene_desc* desc, const snerg_bak
     P.n_blob = field->n_blob;
     const int B3 = desc->B * desc->B * desc->B;
     P.item_voxels = B3 < kThreads ? B3 : kThreads;
+    P.alpha_codes = (desc->flags & SNERG_FLAG_ALPHA_ATLAS) ? 1 : 0;
     P.lg_items = ilog2_exact(B3 / P.item_voxels);
     const double v = (double)desc->extent / (double)desc->N;
     P.v = (float)v;

@@ -70,6 +70,8 @@ struct DevScene {
     float bmin[3];
     float kappa;      // binary32(sigma_max * extent / N / 255): optical depth per density code
     float taumax;     // binary32(ln 1000)
+    float tmin;       // alpha atlas: binary32(1e-3), the exit threshold on T
+    float inv255;     // binary32(1 / 255)
     float bg[3];
     int32_t kmax;     // lattice index cap (4N + 16)
     int32_t flags;    // SNERG_FLAG_*
@@ -400,12 +402,24 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             const float e0 = __fadd_rn(__fmul_rn(e00, g[1]), __fmul_rn(e10, f[1]));
             const float e1 = __fadd_rn(__fmul_rn(e01, g[1]), __fmul_rn(e11, f[1]));
             const float sq = __fadd_rn(__fmul_rn(e0, g[2]), __fmul_rn(e1, f[2]));
-            const float od = __fmul_rn(sq, s.kappa);
-            st.tau = __fadd_rn(st.tau, od);
             // compositing (Eqs. 2, 5, 6)
-            const float e = expf(-od);
-            const float wk = st.T * (1.0f - e);
-            st.T *= e;
+            float wk;
+            bool saturated;
+            if (s.flags & SNERG_FLAG_ALPHA_ATLAS) {
+                // channel 0 holds alpha: a = s * binary32(1/255), T <- T (1 - a) in binary32,
+                // stop once T < binary32(1e-3)
+                const float a = __fmul_rn(sq, s.inv255);
+                wk = st.T * a;
+                st.T = __fmul_rn(st.T, __fsub_rn(1.0f, a));
+                saturated = st.T < s.tmin;
+            } else {
+                const float od = __fmul_rn(sq, s.kappa);
+                st.tau = __fadd_rn(st.tau, od);
+                const float e = expf(-od);
+                wk = st.T * (1.0f - e);
+                st.T *= e;
+                saturated = st.tau > s.taumax;
+            }
             accumulate_colour(st, cv, wk, f, g);
             if (PS) {
                 // this sample's own decoded colour and features, then its residual
@@ -451,7 +465,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                               make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
                 }
             }
-            if (st.tau > s.taumax) {
+            if (saturated) {
                 st.steps += kk - k + 1;
                 done = true;
                 break;

@@ -275,6 +275,8 @@ extern "C" snerg_status snerg_render_rays_noalloc(const snerg_scene_desc* desc, 
         }
         s.kappa = (float)((double)desc->sigma_max * ((double)desc->extent / (double)N) / 255.0);
         s.taumax = (float)std::log(1000.0);
+        s.tmin = (float)1e-3;
+        s.inv255 = (float)(1.0 / 255.0);
         s.flags = desc->flags;
         s.kmax = desc->max_steps > 0 ? (desc->max_steps < 4 * N + 16 ? desc->max_steps : 4 * N + 16) : 4 * N + 16;
         render_rays_noalloc_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(

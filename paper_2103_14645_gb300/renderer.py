@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libsnerg.so")
 MLP_PARAMS = 883
 FLAG_UNPREMULTIPLY = 1
 FLAG_PER_SAMPLE_MLP = 2
+FLAG_ALPHA_ATLAS = 4
 MAX_CAMERAS = 256
 AUX_CH = 8
 
@@ -431,16 +432,17 @@ def bake_field(blobs, colors, jitter, tau_alpha: float = 0.005) -> BakeField:
 
 
 def bake(N: int, B: int, bmin, extent: float, sigma_max: float, field: BakeField, device="cuda",
-         max_blocks: int | None = None):
+         max_blocks: int | None = None, flags: int = 0):
     """Bake an analytic field into (indirection int32 [G,G,G], atlas uint8 [nb,B,B,B,8]) on
     the GPU with snerg_bake (Sec. 5.3-5.4). With max_blocks None the atlas is sized by a
-    first call that only counts the kept blocks."""
+    first call that only counts the kept blocks. flags = FLAG_ALPHA_ATLAS stores alpha
+    codes in channel 0."""
     lib = load_library()
     device = torch.device(device)
     if device.type != "cuda":
         raise ValueError("bake needs a CUDA device")
     desc = SceneDesc(int(N), int(B), (ctypes.c_float * 3)(*bmin), float(extent), float(sigma_max),
-                     (ctypes.c_float * 3)(0, 0, 0), 0, 0)
+                     (ctypes.c_float * 3)(0, 0, 0), 0, int(flags))
     nbytes = lib.snerg_bake_workspace_bytes(ctypes.byref(desc))
     if nbytes == 0:
         raise ValueError("invalid scene description for baking")

@@ -176,3 +176,37 @@ def test_bake_paper_scale_sampled():
     sel = flat[sample] >= 0
     ndiff = _compare_blocks(atl_g[flat[sample][sel]], content[sel], raw[sel])
     assert ndiff <= 1e-4 * content[sel].size + 2
+
+
+def test_bake_alpha_codes_match_oracle_and_render():
+    """With the alpha-atlas flag the bake stores alpha = 1 - exp(-sigma v) codes; they match
+    the oracle (rounding band), and the baked grid renders in alpha mode like the oracle's."""
+    N, B, sigma_max = 64, 8, 120.0
+    f = synth.analytic_field(31, n_blob=24, std=(0.04, 0.12), peak=(10.0, 120.0))
+    field = renderer.bake_field(f["blobs"], f["colors"], f["jitter"], TAU)
+    ind, atl = renderer.bake(N, B, BMIN, EXTENT, sigma_max, field, DEV, flags=renderer.FLAG_ALPHA_ATLAS)
+    ind_g, atl_g = ind.cpu().numpy(), atl.cpu().numpy()
+    ind_o, atl_o, amax = oracle.bake(N, B, BMIN, EXTENT, sigma_max, f["blobs"], f["colors"], f["jitter"],
+                                     alpha_codes=True)
+    ambiguous = np.abs(amax - TAU) <= 5e-5 * TAU
+    assert (((ind_g >= 0) == (ind_o >= 0)) | ambiguous).all()
+    both = (ind_g >= 0) & (ind_o >= 0)
+    blocks = np.flatnonzero(both.ravel())
+    _, content, raw = oracle.bake_blocks(N, B, BMIN, EXTENT, sigma_max, f["blobs"], f["colors"], f["jitter"], blocks,
+                                         alpha_codes=True)
+    np.testing.assert_array_equal(content, atl_o[ind_o.ravel()[blocks]])
+    _compare_blocks(atl_g[ind_g.ravel()[blocks]], content, raw)
+    assert (atl_g[..., 0] > 0).mean() > 0.2
+    if np.array_equal(ind_g, ind_o) and np.array_equal(atl_g, atl_o):
+        rng = np.random.default_rng(6)
+        cams = synth.orbit_cameras(rng, [(40, 40)], synth.CAM_RADIUS)
+        mlp = synth.init_mlp(rng)
+        sc = synth.custom_scene(N, B, ind_o, atl_o, sigma_max, mlp, cams, bmin=BMIN, extent=EXTENT,
+                                flags=renderer.FLAG_ALPHA_ATLAS)
+        r = renderer.Renderer.from_scene(sc, DEV)
+        pix = synth.all_pixels(cams)
+        got = r.render_rays(cams, torch.from_numpy(pix).to(DEV), torch.from_numpy(mlp).to(DEV), counts=True)
+        r.check_status()
+        ref = oracle.render_rays(sc, pix)
+        np.testing.assert_array_equal(got["counts"].cpu().numpy()[:, :2], ref["counts"])
+        assert np.abs(got["rgb"].cpu().numpy() - ref["rgb"]).max() <= 1e-4

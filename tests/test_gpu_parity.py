@@ -604,3 +604,71 @@ def test_per_sample_model_unsupported_paths():
     with pytest.raises((ValueError, renderer.SnergError)):
         renderer.Renderer(sc0.N, sc0.B, sc0.bmin, sc0.extent, sc0.sigma_max, sc0.bg,
                           torch.from_numpy(sc0.ind).to(DEV), torch.from_numpy(sc0.atlas).to(DEV), flags=3)
+
+
+# --------------------------------------------------------------------------------------
+# alpha atlas (channel 0 holds alpha codes, App. A's alpha texture)
+# --------------------------------------------------------------------------------------
+
+def _alpha(name, extra=0):
+    sc0 = scene(name)
+    return synth.custom_scene(sc0.N, sc0.B, sc0.ind, sc0.atlas, sc0.sigma_max, sc0.mlp, sc0.cameras,
+                              flags=renderer.FLAG_ALPHA_ATLAS | extra)
+
+
+@pytest.mark.parametrize("name,extra", [("tiny", 0), ("gauss64", 0), ("gauss64", renderer.FLAG_UNPREMULTIPLY)])
+def test_alpha_atlas_forward_parity(name, extra):
+    """Counts and visited voxels bit-exact (the binary32 running product decides the exit),
+    colours within 1e-4, through the image, persistent and ray-list paths."""
+    sc = _alpha(name, extra)
+    g, r = gpu_render(sc, aux=True, counts=True, trace_cap=64)
+    o = oracle_all(sc, trace_cap=64)
+    assert o["counts"][:, 1].max() <= 64
+    assert_parity(g, o)
+    dens = oracle_all(scene(name))
+    assert np.abs(o["rgb"] - dens["rgb"]).max() > 1e-2              # the flag changes the image
+    r.set_mlp(sc.mlp)
+    got = r.render(sc.cameras, None, persistent=True, tile=(8, 4), ctas_per_sm=2).cpu().numpy()
+    assert np.abs(got - o["rgb"]).max() <= TOL
+    pix = synth.all_pixels(sc.cameras)
+    rr = r.render_rays(sc.cameras, torch.from_numpy(pix).to(DEV), torch.from_numpy(sc.mlp).to(DEV)).cpu().numpy()
+    r.check_status()
+    assert np.abs(rr - o["rgb"]).max() <= TOL
+
+
+def test_alpha_atlas_paper_scale_view():
+    """The 1024^3 grid read as an alpha atlas, the full 800x800 view: every pixel's counts
+    and colour."""
+    sc = _alpha("shell1024")
+    r = renderer.Renderer.from_scene(sc, DEV)
+    r.set_mlp(sc.mlp)
+    out = r.render(sc.cameras, None, counts=True)
+    r.check_status()
+    o = oracle_all(sc)
+    np.testing.assert_array_equal(out["counts"].cpu().numpy()[:, :2], o["counts"])
+    assert np.abs(out["rgb"].cpu().numpy() - o["rgb"]).max() <= TOL
+
+
+def test_alpha_atlas_backward_parity():
+    sc = _alpha("gauss64")
+    pix, g = _bwd_case(sc, 4096, 61)
+    ga, gm, r = gpu_backward(sc, pix, g)
+    ra, rm = oracle.backward_rays(sc, pix, g)
+    assert np.abs(ga - ra).max() <= 1e-4 * np.abs(ra).max()
+    assert np.abs(gm - rm).max() <= 1e-4 * np.abs(rm).max()
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    pt = torch.from_numpy(pix).to(DEV)
+    fwd = r.render_rays(sc.cameras, pt, w, aux=True, counts=True)
+    ga2 = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=DEV)
+    gm2 = torch.zeros(883, dtype=torch.float32, device=DEV)
+    r.backward(sc.cameras, pt, w, torch.from_numpy(g).to(DEV), ga2, gm2, fwd_aux=fwd["aux"], fwd_counts=fwd["counts"])
+    r.check_status()
+    assert np.abs(ga2.cpu().numpy() - ra).max() <= 1e-4 * np.abs(ra).max()
+
+
+def test_alpha_atlas_per_sample_model():
+    sc = _alpha("gauss64", renderer.FLAG_PER_SAMPLE_MLP)
+    g, _ = gpu_render(sc, aux=True, counts=True)
+    o = oracle_all(sc)
+    np.testing.assert_array_equal(g["counts"][:, :2], o["counts"])
+    assert np.abs(g["rgb"] - o["rgb"]).max() <= TOL

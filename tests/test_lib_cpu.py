@@ -64,7 +64,7 @@ def test_workspace_bytes(lib):
     neg = _desc()
     neg.max_steps = -1
     badflag = _desc()
-    badflag.flags = 4                # undefined bit
+    badflag.flags = 8                # undefined bit
     combo = _desc()
     combo.flags = 3                  # un-premultiply belongs to the deferred model
     for bad in [_desc(64, 6), _desc(60, 8), _desc(64, 8, extent=0.0), _desc(64, 8, sigma=float("nan")),
@@ -90,6 +90,10 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.snerg_render_backward(None, cams.ctypes.data, 1, None, 0, None, None, None, None, None, None, None) == 1
     assert lib.snerg_last_status(None, None) == 1
     assert lib.snerg_requantize_atlas(None, 256, None, None) == 1
+    alpha = _desc()
+    alpha.flags = 4                  # the allocation-free entry point renders density atlases only
+    assert lib.snerg_render_rays_noalloc(ctypes.byref(alpha), 256, 256, 1, cams.ctypes.data, 1, 256, 1, 256, 256,
+                                         None, None) == 1
     assert lib.snerg_launch_count(None) == 0
     lib.snerg_destroy(None)
 
