@@ -183,6 +183,25 @@ snerg_status snerg_render_backward(snerg_handle h, const snerg_camera* cams, int
                                    const int32_t* d_fwd_counts, float* d_grad_atlas,
                                    float* d_grad_mlp, void* stream);
 
+/* Data-parallel fine-tuning (one exchange step per training step, Sec. 5.5 run on several
+ * GPUs): every rank sums dL/dPhi and the atlas gradient of its own rays, and the ranks
+ * all-reduce them before the optimiser step. The atlas gradient is exchanged only over the
+ * macroblocks some rank touched; these three calls prepare that exchange (the all-reduce
+ * itself is the caller's, e.g. NCCL). block_floats = floats per block (B^3 * 8), a
+ * multiple of 4; device pointers 16-byte aligned; asynchronous on `stream`.
+ *   snerg_grad_blocks_touched : d_mask[b] = 1 if any of block b's floats is non-zero, else 0
+ *                               (d_grad [num_blocks][block_floats], d_mask int32 [num_blocks]);
+ *   snerg_grad_blocks_gather  : d_packed[i] = d_grad[d_list[i]] for i < n (whole blocks);
+ *   snerg_grad_blocks_scatter : d_grad[d_list[i]] = d_packed[i] for i < n.
+ * List entries must lie in [0, num_blocks) of the gradient they index and, for the
+ * scatter, be distinct. */
+snerg_status snerg_grad_blocks_touched(const float* d_grad, int64_t num_blocks, int32_t block_floats,
+                                       int32_t* d_mask, void* stream);
+snerg_status snerg_grad_blocks_gather(const float* d_grad, const int32_t* d_list, int64_t n, int32_t block_floats,
+                                      float* d_packed, void* stream);
+snerg_status snerg_grad_blocks_scatter(const float* d_packed, const int32_t* d_list, int64_t n,
+                                       int32_t block_floats, float* d_grad, void* stream);
+
 /* Requantise fine-tuned colour and feature values into the scene. The paper fine-tunes the
  * view-dependence MLP against the training images (Sec. 5.5); the baked colours and
  * features can be fine-tuned the same way through an FP32 shadow copy that takes the

@@ -48,6 +48,35 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, float*
     }
 }
 
+// Data-parallel fine-tuning exchanges the atlas gradient only over the macroblocks some
+// rank touched: a per-block "any non-zero" mask, then the touched blocks gathered into a
+// packed buffer for the all-reduce and scattered back.
+__global__ void __launch_bounds__(256) block_touched_kernel(const float4* __restrict__ g, int64_t nb, int32_t bf4,
+                                                            int32_t* __restrict__ mask) {
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        bool nz = false;
+        for (int32_t i = threadIdx.x; i < bf4; i += blockDim.x) {
+            const float4 v = g[b * bf4 + i];
+            nz |= (v.x != 0.0f) | (v.y != 0.0f) | (v.z != 0.0f) | (v.w != 0.0f);
+        }
+        const int any = __syncthreads_or(nz);
+        if (threadIdx.x == 0) mask[b] = any ? 1 : 0;
+    }
+}
+
+// dst[i] = src[list[i]] (gather) or dst[list[i]] = src[i] (scatter), bf4 float4 per block
+template <bool GATHER>
+__global__ void __launch_bounds__(256) block_copy_kernel(const float4* __restrict__ src,
+                                                         const int32_t* __restrict__ list, int64_t n, int32_t bf4,
+                                                         float4* __restrict__ dst) {
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const int64_t b = list[i];
+        const float4* s = src + (GATHER ? b : i) * bf4;
+        float4* d = dst + (GATHER ? i : b) * bf4;
+        for (int32_t j = threadIdx.x; j < bf4; j += blockDim.x) d[j] = s[j];
+    }
+}
+
 static unsigned grid_1d(int64_t n) {
     const int64_t b = (n + 255) / 256;
     return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -76,5 +105,40 @@ extern "C" snerg_status snerg_adam_step(float* d_param, float* d_m, float* d_v, 
     const float c2 = (float)(1.0 - std::pow((double)beta2, (double)step));
     adam_kernel<<<grid_1d(n), 256, 0, (cudaStream_t)stream>>>(d_param, d_m, d_v, d_grad, n, lr, beta1, beta2, eps,
                                                               c1, c2);
+    return cudaGetLastError() == cudaSuccess ? SNERG_OK : SNERG_E_CUDA;
+}
+
+static bool block_args_ok(const void* a, const void* b, int64_t n, int32_t block_floats) {
+    if (n < 0 || block_floats <= 0 || (block_floats & 3)) return false;
+    if (n > 0 && (!a || !b || ((uintptr_t)a & 15u) || ((uintptr_t)b & 15u))) return false;
+    return true;
+}
+
+static unsigned grid_blocks(int64_t n) { return (unsigned)(n < 65535 ? (n > 0 ? n : 1) : 65535); }
+
+extern "C" snerg_status snerg_grad_blocks_touched(const float* d_grad, int64_t num_blocks, int32_t block_floats,
+                                                  int32_t* d_mask, void* stream) {
+    if (!block_args_ok(d_grad, d_mask, num_blocks, block_floats)) return SNERG_E_INVAL;
+    if (num_blocks == 0) return SNERG_OK;
+    block_touched_kernel<<<grid_blocks(num_blocks), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float4*>(d_grad), num_blocks, block_floats / 4, d_mask);
+    return cudaGetLastError() == cudaSuccess ? SNERG_OK : SNERG_E_CUDA;
+}
+
+extern "C" snerg_status snerg_grad_blocks_gather(const float* d_grad, const int32_t* d_list, int64_t n,
+                                                 int32_t block_floats, float* d_packed, void* stream) {
+    if (!block_args_ok(d_grad, d_packed, n, block_floats) || (n > 0 && !d_list)) return SNERG_E_INVAL;
+    if (n == 0) return SNERG_OK;
+    block_copy_kernel<true><<<grid_blocks(n), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float4*>(d_grad), d_list, n, block_floats / 4, reinterpret_cast<float4*>(d_packed));
+    return cudaGetLastError() == cudaSuccess ? SNERG_OK : SNERG_E_CUDA;
+}
+
+extern "C" snerg_status snerg_grad_blocks_scatter(const float* d_packed, const int32_t* d_list, int64_t n,
+                                                  int32_t block_floats, float* d_grad, void* stream) {
+    if (!block_args_ok(d_packed, d_grad, n, block_floats) || (n > 0 && !d_list)) return SNERG_E_INVAL;
+    if (n == 0) return SNERG_OK;
+    block_copy_kernel<false><<<grid_blocks(n), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float4*>(d_packed), d_list, n, block_floats / 4, reinterpret_cast<float4*>(d_grad));
     return cudaGetLastError() == cudaSuccess ? SNERG_OK : SNERG_E_CUDA;
 }

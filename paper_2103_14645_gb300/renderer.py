@@ -30,7 +30,8 @@ EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_rend
             "snerg_render_backward", "snerg_last_status", "snerg_launch_count",
             "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc",
             "snerg_set_mlp", "snerg_l2_loss", "snerg_adam_step", "snerg_bake_workspace_bytes", "snerg_bake",
-            "snerg_requantize_atlas"]
+            "snerg_requantize_atlas", "snerg_grad_blocks_touched", "snerg_grad_blocks_gather",
+            "snerg_grad_blocks_scatter"]
 MAX_BAKE_BLOBS = 64
 
 
@@ -100,6 +101,12 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_set_mlp.restype = ctypes.c_int
     lib.snerg_render_rays_noalloc.argtypes = [P, P, P, i64, P, i32, P, i64, P, P, P, P]
     lib.snerg_render_rays_noalloc.restype = ctypes.c_int
+    lib.snerg_grad_blocks_touched.argtypes = [P, i64, i32, P, P]
+    lib.snerg_grad_blocks_touched.restype = ctypes.c_int
+    lib.snerg_grad_blocks_gather.argtypes = [P, P, i64, i32, P, P]
+    lib.snerg_grad_blocks_gather.restype = ctypes.c_int
+    lib.snerg_grad_blocks_scatter.argtypes = [P, P, i64, i32, P, P]
+    lib.snerg_grad_blocks_scatter.restype = ctypes.c_int
     lib.snerg_requantize_atlas.argtypes = [P, P, P, P]
     lib.snerg_requantize_atlas.restype = ctypes.c_int
     lib.snerg_bake_workspace_bytes.argtypes = [P]
@@ -362,6 +369,55 @@ def adam_step(param: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch
                                float(betas[1]), float(eps), int(step), _stream(param.device)), "snerg_adam_step")
 
 
+class GpuBlockOps:
+    """The library's kernels behind the touched-block exchange of atlas gradients."""
+
+    @staticmethod
+    def touched(grad_atlas: torch.Tensor) -> torch.Tensor:
+        nb = int(grad_atlas.shape[0])
+        bf = grad_atlas[0].numel() if nb else 0
+        mask = torch.empty(nb, dtype=torch.int32, device=grad_atlas.device)
+        _check(load_library().snerg_grad_blocks_touched(_ptr(grad_atlas), nb, bf, _ptr(mask),
+                                                        _stream(grad_atlas.device)), "snerg_grad_blocks_touched")
+        return mask
+
+    @staticmethod
+    def gather(grad_atlas: torch.Tensor, idx: torch.Tensor) -> torch.Tensor:
+        bf = grad_atlas[0].numel()
+        packed = torch.empty((idx.numel(), bf), dtype=torch.float32, device=grad_atlas.device)
+        _check(load_library().snerg_grad_blocks_gather(_ptr(grad_atlas), _ptr(idx), idx.numel(), bf, _ptr(packed),
+                                                       _stream(grad_atlas.device)), "snerg_grad_blocks_gather")
+        return packed
+
+    @staticmethod
+    def scatter(packed: torch.Tensor, idx: torch.Tensor, grad_atlas: torch.Tensor):
+        bf = grad_atlas[0].numel()
+        _check(load_library().snerg_grad_blocks_scatter(_ptr(packed), _ptr(idx), idx.numel(), bf, _ptr(grad_atlas),
+                                                        _stream(grad_atlas.device)), "snerg_grad_blocks_scatter")
+
+
+def allreduce_gradients(grad_mlp: torch.Tensor, grad_atlas: torch.Tensor | None = None, group=None,
+                        ops=GpuBlockOps) -> int:
+    """The exchange step of data-parallel fine-tuning: sum dL/dPhi over the ranks, and the
+    atlas gradient over the union of the macroblocks any rank touched (mask all-reduced
+    with MAX, touched blocks packed, summed, scattered back; blocks no rank touched stay
+    zero on every rank). Returns the number of blocks exchanged. `ops` supplies the
+    touched-mask / gather / scatter steps (the library's kernels by default)."""
+    import torch.distributed as dist
+    dist.all_reduce(grad_mlp, group=group)
+    if grad_atlas is None or grad_atlas.shape[0] == 0:
+        return 0
+    mask = ops.touched(grad_atlas)
+    dist.all_reduce(mask, op=dist.ReduceOp.MAX, group=group)
+    idx = torch.nonzero(mask).flatten().to(torch.int32).contiguous()
+    if idx.numel() == 0:
+        return 0
+    packed = ops.gather(grad_atlas, idx)
+    dist.all_reduce(packed, group=group)
+    ops.scatter(packed, idx, grad_atlas)
+    return int(idx.numel())
+
+
 class FineTuner:
     """Fine-tunes the view-dependence MLP of a baked grid against observed pixels with
     Adam and the L2 loss, as the paper does after baking (Sec. 5.5: Adam, learning rate
@@ -371,11 +427,17 @@ class FineTuner:
     With `atlas` (the scene's uint8 atlas [nb,B,B,B,8]) and `atlas_lr`, the baked colours
     and features are fine-tuned too: an FP32 shadow copy (q / 255) takes Adam steps on the
     backward's atlas gradient (zero on the density channel, which stays frozen) and is
-    requantised into the scene's 8-bit codes after every step."""
+    requantised into the scene's 8-bit codes after every step.
+
+    Data parallel: when torch.distributed is initialised with more than one rank (or
+    `group` names such a group), each rank passes its own rays and the gradients are summed
+    over the ranks (allreduce_gradients) before the identical optimiser step on every rank;
+    the returned loss is the rank's own."""
 
     def __init__(self, renderer: Renderer, mlp, lr: float = 3e-4, betas=(0.9, 0.999), eps: float = 1e-8,
-                 atlas=None, atlas_lr: float | None = None):
+                 atlas=None, atlas_lr: float | None = None, group=None):
         self.r = renderer
+        self.group = group
         self.mlp = torch.as_tensor(np.asarray(mlp, np.float32)).to(renderer.device).contiguous()
         self.m = torch.zeros_like(self.mlp)
         self.v = torch.zeros_like(self.mlp)
@@ -408,12 +470,19 @@ class FineTuner:
             self.grad_atlas.zero_()
             ga = self.grad_atlas
         self.r.backward(cams, pix, self.mlp, g, ga, self.grad, fwd_aux=fwd["aux"], fwd_counts=fwd["counts"])
+        if _data_parallel(self.group):
+            allreduce_gradients(self.grad, ga, self.group)
         self.steps += 1
         adam_step(self.mlp, self.m, self.v, self.grad, self.steps, self.lr, self.betas, self.eps)
         if self.shadow is not None:
             adam_step(self.shadow, self.ma, self.va, self.grad_atlas, self.steps, self.atlas_lr, self.betas, self.eps)
             self.r.requantize_atlas(self.shadow, self.codes)
         return self.loss
+
+
+def _data_parallel(group) -> bool:
+    import torch.distributed as dist
+    return dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1
 
 
 def bake_field(blobs, colors, jitter, tau_alpha: float = 0.005) -> BakeField:

@@ -159,3 +159,25 @@ def test_finetune_with_shadow_atlas_matches_oracle_reference():
     for c in got_codes:
         np.testing.assert_array_equal(c[..., 0], sc.atlas[..., 0])
     assert losses[-1] < losses[0]
+
+
+def test_gradient_block_exchange_kernels():
+    """The touched-block mask, gather and scatter kernels of the data-parallel exchange
+    against plain tensor indexing."""
+    rng = np.random.default_rng(9)
+    nb, B = 37, 8
+    g = rng.normal(size=(nb, B, B, B, 8)).astype(np.float32)
+    zero = rng.choice(nb, 15, replace=False)
+    g[zero] = 0.0
+    g[zero[0], 3, 2, 1, 5] = -1e-30                       # one non-zero value keeps a block
+    tg = torch.from_numpy(g).to(DEV)
+    mask = renderer.GpuBlockOps.touched(tg).cpu().numpy()
+    np.testing.assert_array_equal(mask, (g.reshape(nb, -1) != 0).any(1).astype(np.int32))
+    idx = torch.from_numpy(np.flatnonzero(mask).astype(np.int32)).to(DEV)
+    packed = renderer.GpuBlockOps.gather(tg, idx)
+    np.testing.assert_array_equal(packed.cpu().numpy(), g.reshape(nb, -1)[np.flatnonzero(mask)])
+    out = torch.zeros_like(tg)
+    renderer.GpuBlockOps.scatter(packed * 2.0, idx, out)
+    want = np.zeros_like(g)
+    want[np.flatnonzero(mask)] = 2.0 * g[np.flatnonzero(mask)]
+    np.testing.assert_array_equal(out.cpu().numpy(), want)

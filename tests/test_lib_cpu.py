@@ -90,6 +90,11 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.snerg_render_backward(None, cams.ctypes.data, 1, None, 0, None, None, None, None, None, None, None) == 1
     assert lib.snerg_last_status(None, None) == 1
     assert lib.snerg_requantize_atlas(None, 256, None, None) == 1
+    assert lib.snerg_grad_blocks_touched(256, 4, 6, 256, None) == 1          # block_floats not a multiple of 4
+    assert lib.snerg_grad_blocks_touched(260, 4, 8, 256, None) == 1          # misaligned
+    assert lib.snerg_grad_blocks_gather(256, None, 3, 8, 256, None) == 1     # no list
+    assert lib.snerg_grad_blocks_scatter(256, 256, -1, 8, 256, None) == 1
+    assert lib.snerg_grad_blocks_gather(None, None, 0, 8, None, None) == 0   # nothing to do
     alpha = _desc()
     alpha.flags = 4                  # the allocation-free entry point renders density atlases only
     assert lib.snerg_render_rays_noalloc(ctypes.byref(alpha), 256, 256, 1, cams.ctypes.data, 1, 256, 1, 256, 256,
