@@ -109,6 +109,13 @@ typedef struct {
                               captured into a CUDA graph on first use and replayed */
     int32_t tile_w, tile_h;/* persistent only: pixel tile per work item; 0 = autotune */
     int32_t ctas_per_sm;   /* persistent only: 0 = autotune */
+    int32_t row_begin;     /* snerg_render without persistent: render only image rows
+                              [row_begin, row_end) of every camera (clamped to its H), with
+                              exactly the rays of the full render; other pixels of d_rgb
+                              are not written. 0, 0 = all rows. Lets a caller split a frame
+                              into bands on several streams and copy each band out as soon
+                              as it is done. */
+    int32_t row_end;
 } snerg_render_opts;
 
 /* Largest number of cameras in one snerg_render / ray-list call. */
@@ -157,6 +164,20 @@ snerg_status snerg_set_mlp(snerg_handle h, const float* mlp);
 snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
                           const float* d_mlp, float* d_rgb, const snerg_render_opts* opts,
                           void* stream);
+
+/* Render every pixel of n_cams cameras and deliver the image to host memory, overlapping
+ * the device-to-host copy with the render: the rows are split into n_bands bands
+ * (1..16; the rows of every camera, by the tallest camera's height), each band is rendered
+ * on one of the handle's side streams (created by the first call) after the work already
+ * queued on `stream`, and copied to h_rgb as soon as it is done; `stream` then waits for
+ * every band, so h_rgb is complete once `stream` is synchronised. The rays and colours are
+ * those of snerg_render (plain launch).
+ *   d_rgb : float32 device image [pixels][3] through out_offset (the render's output);
+ *   h_rgb : HOST float32 [pixels][3] through out_offset; page-locked memory makes the
+ *           copies asynchronous, so that they overlap the rest of the render.
+ * d_mlp as for snerg_render (NULL = the snerg_set_mlp weights). */
+snerg_status snerg_render_to_host(snerg_handle h, const snerg_camera* cams, int32_t n_cams, const float* d_mlp,
+                                  float* d_rgb, float* h_rgb, int32_t n_bands, void* stream);
 
 /* Render a list of rays: d_pix int32 [n][3] = (camera index, x, y). Output row i of
  * d_rgb (and of the optional opts outputs) belongs to ray i; out_offset is ignored.

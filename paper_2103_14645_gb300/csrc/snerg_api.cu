@@ -115,6 +115,9 @@ struct snerg_scene {
     PersistentConfig last{0, 0, 0, 0, 0};
     MlpWeights host_w;        // snerg_set_mlp: weights in the transposed kernel layout
     bool has_w = false;
+    std::vector<cudaStream_t> band_streams;   // snerg_render_to_host: one per band
+    std::vector<cudaEvent_t> band_done;
+    cudaEvent_t band_fork = nullptr;
 };
 
 extern "C" size_t snerg_workspace_bytes(const snerg_scene_desc* desc, int64_t num_blocks) {
@@ -406,18 +409,74 @@ extern "C" snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, i
     if (!d_rgb || (!d_mlp && !h->has_w)) return SNERG_E_INVAL;
     const MlpWeights* pw = d_mlp ? nullptr : &h->host_w;
     cudaStream_t st = (cudaStream_t)stream;
+    const bool rows = opts && (opts->row_begin != 0 || opts->row_end != 0);
+    if (rows && (opts->row_begin < 0 || opts->row_end < opts->row_begin)) return SNERG_E_INVAL;
     if (opts && opts->persistent && !opts_debug(opts)) {
         if (h->desc.flags & SNERG_FLAG_PER_SAMPLE_MLP) return SNERG_E_UNSUPPORTED;
+        if (rows) return SNERG_E_UNSUPPORTED;
         return render_persistent(h, cams, n_cams, d_mlp, pw, d_rgb, opts, st);
     }
     const DebugOut dbg = make_dbg(opts);
     for (int i = 0; i < n_cams; ++i) {
         if (cams[i].W == 0 || cams[i].H == 0) continue;
-        cudaError_t e = launch_render_image(h->ds, cams[i], d_mlp, pw, d_rgb, dbg, st);
+        const int r0 = rows ? opts->row_begin : 0, r1 = rows ? opts->row_end : cams[i].H;
+        if (std::min(r1, cams[i].H) <= r0) continue;
+        cudaError_t e = launch_render_image(h->ds, cams[i], d_mlp, pw, d_rgb, dbg, st, r0, r1);
         if (e != cudaSuccess) return SNERG_E_CUDA;
         h->launches++;
     }
     return SNERG_OK;
+}
+
+constexpr int kMaxBands = 16;
+
+extern "C" snerg_status snerg_render_to_host(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
+                                             const float* d_mlp, float* d_rgb, float* h_rgb, int32_t n_bands,
+                                             void* stream) {
+    if (!h || !cams || n_cams < 1 || n_cams > kMaxCams || n_bands < 1 || n_bands > kMaxBands) return SNERG_E_INVAL;
+    int64_t pixels = 0;
+    int Hmax = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        if (!camera_ok(cams[i])) return SNERG_E_INVAL;
+        pixels += (int64_t)cams[i].W * cams[i].H;
+        Hmax = std::max(Hmax, cams[i].H);
+    }
+    if (pixels == 0) return SNERG_OK;
+    if (!d_rgb || !h_rgb || (!d_mlp && !h->has_w)) return SNERG_E_INVAL;
+    const MlpWeights* pw = d_mlp ? nullptr : &h->host_w;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!h->band_fork) e = cudaEventCreateWithFlags(&h->band_fork, cudaEventDisableTiming);
+    while (e == cudaSuccess && (int)h->band_streams.size() < n_bands) {
+        cudaStream_t b = nullptr;
+        cudaEvent_t d = nullptr;
+        e = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking);
+        if (e == cudaSuccess) h->band_streams.push_back(b);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
+        if (e == cudaSuccess) h->band_done.push_back(d);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(h->band_fork, st);
+    const DebugOut dbg{nullptr, nullptr, nullptr, 0};
+    n_bands = std::min(n_bands, Hmax);
+    for (int b = 0; b < n_bands && e == cudaSuccess; ++b) {
+        const int y0 = (int)((int64_t)Hmax * b / n_bands), y1 = (int)((int64_t)Hmax * (b + 1) / n_bands);
+        cudaStream_t bs = h->band_streams[b];
+        e = cudaStreamWaitEvent(bs, h->band_fork, 0);
+        for (int i = 0; i < n_cams && e == cudaSuccess; ++i) {
+            const snerg_camera& c = cams[i];
+            const int r0 = std::min(y0, c.H), r1 = std::min(y1, c.H);
+            if (c.W == 0 || r1 <= r0) continue;
+            e = launch_render_image(h->ds, c, d_mlp, pw, d_rgb, dbg, bs, r0, r1);
+            if (e != cudaSuccess) break;
+            h->launches++;
+            const size_t first = (size_t)(c.out_offset + (int64_t)r0 * c.W) * 3;
+            const size_t count = (size_t)(r1 - r0) * c.W * 3;
+            e = cudaMemcpyAsync(h_rgb + first, d_rgb + first, count * sizeof(float), cudaMemcpyDeviceToHost, bs);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->band_done[b], bs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->band_done[b], 0);
+    }
+    return e == cudaSuccess ? SNERG_OK : SNERG_E_CUDA;
 }
 
 static bool make_table(const snerg_camera* cams, int32_t n_cams, CamTable* t) {
@@ -519,6 +578,9 @@ extern "C" void snerg_destroy(snerg_handle h) {
         if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
     }
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (cudaStream_t b : h->band_streams) cudaStreamDestroy(b);
+    for (cudaEvent_t e : h->band_done) cudaEventDestroy(e);
+    if (h->band_fork) cudaEventDestroy(h->band_fork);
     delete h;
 }
 

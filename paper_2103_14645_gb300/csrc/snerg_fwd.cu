@@ -25,7 +25,8 @@ template <bool DBG, bool PW, int NW, bool PS>
 __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const DevScene s, const snerg_camera cam,
                                                                         const float* __restrict__ mlp,
                                                                         const __grid_constant__ MlpWeights pw,
-                                                                        float* __restrict__ rgb, const DebugOut dbg) {
+                                                                        float* __restrict__ rgb, const DebugOut dbg,
+                                                                        int row0, int row1) {
     __shared__ __align__(16) float sW[PW ? 4 : kNParam + 1];
     if (!PW) {
         load_mlp_smem_t(sW, mlp);
@@ -35,8 +36,8 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const De
     using T = ImageTile<NW>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = blockIdx.x * T::TW + (warp % T::WX) * 8 + (lane & 7);
-    const int py = blockIdx.y * T::TH + (warp / T::WX) * 4 + (lane >> 3);
-    if (px >= cam.W || py >= cam.H) return;
+    const int py = row0 + blockIdx.y * T::TH + (warp / T::WX) * 4 + (lane >> 3);
+    if (px >= cam.W || py >= row1) return;
     const Ray r = make_ray(s, cam, px, py);
     const int64_t pix = cam.out_offset + (int64_t)py * cam.W + px;
     MarchState st;
@@ -171,26 +172,29 @@ static const MlpWeights& no_weights() {
 
 template <bool PS>
 static void image_launch(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
-                         float* rgb, const DebugOut& dbg, cudaStream_t st) {
+                         float* rgb, const DebugOut& dbg, cudaStream_t st, int row0, int row1) {
     using T = ImageTile<kImageWarps>;
-    dim3 grid((cam.W + T::TW - 1) / T::TW, (cam.H + T::TH - 1) / T::TH);
+    dim3 grid((cam.W + T::TW - 1) / T::TW, (row1 - row0 + T::TH - 1) / T::TH);
     const int nt = 32 * kImageWarps;
     const bool d = dbg.aux || dbg.counts || dbg.trace;
     const MlpWeights& w = pw ? *pw : no_weights();
     if (pw) {
-        if (d) render_image_kernel<true, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
-        else render_image_kernel<false, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        if (d) render_image_kernel<true, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1);
+        else render_image_kernel<false, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1);
     } else {
-        if (d) render_image_kernel<true, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
-        else render_image_kernel<false, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg);
+        if (d) render_image_kernel<true, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1);
+        else render_image_kernel<false, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1);
     }
 }
 
+// rows [row0, row1) of the camera (clamped to [0, H]); all rows when row1 <= row0 after clamping
 cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
-                                float* rgb, const DebugOut& dbg, cudaStream_t st) {
-    if (cam.W <= 0 || cam.H <= 0) return cudaSuccess;
-    if (s.flags & SNERG_FLAG_PER_SAMPLE_MLP) image_launch<true>(s, cam, mlp, pw, rgb, dbg, st);
-    else image_launch<false>(s, cam, mlp, pw, rgb, dbg, st);
+                                float* rgb, const DebugOut& dbg, cudaStream_t st, int row0, int row1) {
+    row0 = max(row0, 0);
+    row1 = min(row1, cam.H);
+    if (cam.W <= 0 || row1 <= row0) return cudaSuccess;
+    if (s.flags & SNERG_FLAG_PER_SAMPLE_MLP) image_launch<true>(s, cam, mlp, pw, rgb, dbg, st, row0, row1);
+    else image_launch<false>(s, cam, mlp, pw, rgb, dbg, st, row0, row1);
     return cudaGetLastError();
 }
 

@@ -795,7 +795,7 @@ struct DebugOut {
 
 // pw: weights as a kernel parameter (nullptr: read them from `mlp` in device memory)
 cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
-                                float* rgb, const DebugOut& dbg, cudaStream_t st);
+                                float* rgb, const DebugOut& dbg, cudaStream_t st, int row0, int row1);
 cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
                                int64_t n, const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg,
                                cudaStream_t st);

@@ -31,7 +31,7 @@ EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_rend
             "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc",
             "snerg_set_mlp", "snerg_l2_loss", "snerg_adam_step", "snerg_bake_workspace_bytes", "snerg_bake",
             "snerg_requantize_atlas", "snerg_grad_blocks_touched", "snerg_grad_blocks_gather",
-            "snerg_grad_blocks_scatter"]
+            "snerg_grad_blocks_scatter", "snerg_render_to_host"]
 MAX_BAKE_BLOBS = 64
 
 
@@ -50,7 +50,8 @@ class SceneDesc(ctypes.Structure):
 class RenderOpts(ctypes.Structure):
     _fields_ = [("d_aux", ctypes.c_void_p), ("d_counts", ctypes.c_void_p), ("d_trace", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_int32), ("persistent", ctypes.c_int32), ("tile_w", ctypes.c_int32),
-                ("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("row_begin", ctypes.c_int32),
+                ("row_end", ctypes.c_int32)]
 
 
 class BakeField(ctypes.Structure):
@@ -101,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_set_mlp.restype = ctypes.c_int
     lib.snerg_render_rays_noalloc.argtypes = [P, P, P, i64, P, i32, P, i64, P, P, P, P]
     lib.snerg_render_rays_noalloc.restype = ctypes.c_int
+    lib.snerg_render_to_host.argtypes = [P, P, i32, P, P, P, i32, P]
+    lib.snerg_render_to_host.restype = ctypes.c_int
     lib.snerg_grad_blocks_touched.argtypes = [P, i64, i32, P, P]
     lib.snerg_grad_blocks_touched.restype = ctypes.c_int
     lib.snerg_grad_blocks_gather.argtypes = [P, P, i64, i32, P, P]
@@ -243,9 +246,10 @@ class Renderer:
         return o, out
 
     def render(self, cams, mlp: torch.Tensor | None, out: torch.Tensor | None = None, aux=False, counts=False,
-               trace_cap: int = 0, persistent=False, tile=None, ctas_per_sm: int = 0):
+               trace_cap: int = 0, persistent=False, tile=None, ctas_per_sm: int = 0, rows=None):
         """Render every pixel of the cameras into out [pixels, 3] (packed by out_offset).
         mlp: device weights, or None for the weights stored with set_mlp.
+        rows: (begin, end) renders only those image rows of every camera.
         Returns out, or a dict with 'rgb' and the requested debug outputs."""
         c = _cams(cams)
         if mlp is not None:
@@ -258,6 +262,8 @@ class Renderer:
             if out.numel() < 3 * n_pix:
                 raise ValueError("out is too small")
         o, extra = self._opts(n_pix, aux, counts, trace_cap, persistent, tile, ctas_per_sm)
+        if rows is not None:
+            o.row_begin, o.row_end = int(rows[0]), int(rows[1])
         code = self.lib.snerg_render(self.handle, c.ctypes.data, c.shape[0], _ptr(mlp), _ptr(out),
                                      ctypes.byref(o), _stream(self.device))
         _check(code, "snerg_render")
@@ -265,6 +271,34 @@ class Renderer:
             extra["rgb"] = out
             return extra
         return out
+
+    def render_to_host(self, cams, host_out: torch.Tensor, mlp: torch.Tensor | None = None,
+                       out: torch.Tensor | None = None, bands: int = 4):
+        """Render the cameras into pinned host memory host_out [pixels, 3] with
+        snerg_render_to_host: `bands` row bands rendered on the library's side streams, each
+        copied out as soon as it is done, overlapping the rest of the render. Enqueued after
+        the current stream's work; host_out is complete once the current stream is
+        synchronised. `out` is the device image (allocated if None)."""
+        c = _cams(cams)
+        if host_out.device.type != "cpu" or not host_out.is_pinned() or host_out.dtype != torch.float32 \
+                or not host_out.is_contiguous():
+            raise ValueError("host_out must be a contiguous pinned float32 CPU tensor")
+        if mlp is not None:
+            _require_cuda(mlp, "mlp", torch.float32)
+        n_pix = int(max((int(x["out_offset"]) + int(x["W"]) * int(x["H"]) for x in c), default=0))
+        if host_out.numel() < 3 * n_pix:
+            raise ValueError("host_out is too small")
+        if out is None:
+            out = torch.empty((n_pix, 3), dtype=torch.float32, device=self.device)
+        else:
+            _require_cuda(out, "out", torch.float32)
+            if out.numel() < 3 * n_pix:
+                raise ValueError("out is too small")
+        with torch.cuda.device(self.device):
+            code = self.lib.snerg_render_to_host(self.handle, c.ctypes.data, c.shape[0], _ptr(mlp), _ptr(out),
+                                                 host_out.data_ptr(), int(bands), _stream(self.device))
+        _check(code, "snerg_render_to_host")
+        return host_out
 
     def render_rays(self, cams, pix: torch.Tensor, mlp: torch.Tensor | None, out=None, aux=False, counts=False,
                     trace_cap: int = 0):

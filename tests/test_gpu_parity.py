@@ -672,3 +672,68 @@ def test_alpha_atlas_per_sample_model():
     o = oracle_all(sc)
     np.testing.assert_array_equal(g["counts"][:, :2], o["counts"])
     assert np.abs(g["rgb"] - o["rgb"]).max() <= TOL
+
+
+# --------------------------------------------------------------------------------------
+# row bands and the banded render into pinned host memory
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["gauss64", "shell1024"])
+def test_row_bands_reproduce_the_full_render(name):
+    """Bands of rows (ragged edges included) render exactly the pixels of the full launch,
+    bit for bit, and leave the other rows untouched."""
+    sc = scene(name)
+    r = renderer.Renderer.from_scene(sc, DEV)
+    r.set_mlp(sc.mlp)
+    full = r.render(sc.cameras, None).clone()
+    H = int(sc.cameras[0]["H"])
+    W = int(sc.cameras[0]["W"])
+    edges = [0, 1, 13, H // 2 + 3, H - 1, H]
+    out = torch.full_like(full, float("nan"))
+    for y0, y1 in zip(edges[:-1], edges[1:]):
+        r.render(sc.cameras, None, out=out, rows=(y0, y1))
+        torch.cuda.synchronize()
+        img = out.view(H, W, 3)
+        assert torch.equal(img[y0:y1], full.view(H, W, 3)[y0:y1])
+        assert torch.isnan(img[y1:]).all()
+    r.check_status()
+    assert torch.equal(out, full)
+
+
+def test_render_to_host_matches_the_device_render():
+    """The banded render with per-band copies into pinned memory returns the device image
+    exactly, for one camera and for a batch of ragged cameras, with 1, 3 and 8 bands."""
+    sc = scene("gauss64")
+    r = renderer.Renderer.from_scene(sc, DEV)
+    r.set_mlp(sc.mlp)
+    cams = synth.orbit_cameras(np.random.default_rng(12), [(37, 23), (64, 64), (5, 70)], synth.CAM_RADIUS)
+    for cs in (sc.cameras, cams):
+        ref = r.render(cs, None).cpu()
+        for bands in (1, 3, 8, 16):
+            host = torch.full((ref.shape[0], 3), float("nan"), dtype=torch.float32, pin_memory=True)
+            r.render_to_host(cs, host, bands=bands)
+            torch.cuda.current_stream(DEV).synchronize()
+            assert torch.equal(host, ref), bands
+    r.check_status()
+
+
+def test_row_option_errors():
+    sc = scene("tiny")
+    r = renderer.Renderer.from_scene(sc, DEV)
+    r.set_mlp(sc.mlp)
+    for rows, code in (((-1, 4), 1), ((5, 3), 1)):
+        with pytest.raises(renderer.SnergError) as e:
+            r.render(sc.cameras, None, rows=rows)
+        assert e.value.code == code
+    with pytest.raises(renderer.SnergError) as e:
+        r.render(sc.cameras, None, persistent=True, rows=(0, 4))
+    assert e.value.code == 5
+    host = torch.empty((int(sc.cameras[0]["W"]) * int(sc.cameras[0]["H"]), 3), pin_memory=True)
+    for bands in (0, 17):
+        with pytest.raises(renderer.SnergError) as e:
+            r.render_to_host(sc.cameras, host, bands=bands)
+        assert e.value.code == 1
+    out = torch.full((int(sc.cameras[0]["W"]) * int(sc.cameras[0]["H"]), 3), 7.0, device=DEV)
+    r.render(sc.cameras, None, out=out, rows=(int(sc.cameras[0]["H"]) + 5, int(sc.cameras[0]["H"]) + 9))
+    torch.cuda.synchronize()
+    assert (out == 7.0).all()                     # rows beyond the image: nothing written

@@ -114,7 +114,7 @@ def test_camera_record_layout():
     assert synth.CAMERA_DTYPE.itemsize == 80
     assert synth.CAMERA_DTYPE.fields["out_offset"][1] == 72
     assert synth.CAMERA_DTYPE.fields["W"][1] == 64
-    assert ctypes.sizeof(renderer.RenderOpts) == 48
+    assert ctypes.sizeof(renderer.RenderOpts) == 56
     assert ctypes.sizeof(renderer.SceneDesc) == 48
 
 
