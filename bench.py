@@ -306,6 +306,16 @@ def run_ours(args, ws, rank, local):
                                    "mrays_s": round(n_rays / (np.mean(ms_ps) * 1e-3) / 1e6, 3),
                                    "slowdown_vs_deferred": round(float(np.mean(ms_ps)) / t_step, 3)}
         del rps
+        # and without the view-dependence network (the paper's other performance ablation)
+        nm_scene = _synth.custom_scene(sc.N, sc.B, sc.ind, sc.atlas, sc.sigma_max, sc.mlp, sc.cameras,
+                                       flags=renderer.FLAG_NO_MLP)
+        rnm = renderer.Renderer.from_scene(nm_scene, dev)
+        rnm.set_mlp(sc.mlp)
+        ms_nm = time_steps(lambda: rnm.render(cams, None, out=out), max(3, min(args.steps, 10)), 2, stream, flush)
+        extra["no_mlp"] = {"ms_per_frame": round(float(np.mean(ms_nm)), 4),
+                           "mrays_s": round(n_rays / (np.mean(ms_nm) * 1e-3) / 1e6, 3),
+                           "deferred_over_no_mlp": round(t_step / float(np.mean(ms_nm)), 3)}
+        del rnm
     clocks = sampler.stop()
 
     if rank != 0:

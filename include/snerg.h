@@ -85,6 +85,10 @@ typedef struct {
  * the probe (code 0 = empty) and all entry points but snerg_render_rays_noalloc work
  * unchanged. snerg_bake with this flag stores alpha = 1 - exp(-sigma v) in channel 0. */
 #define SNERG_FLAG_ALPHA_ATLAS 4
+/* The paper's performance ablation without the view-dependence network (Sec. 6): the
+ * pixel is C_d + T bg; the MLP weights are not read, and the adjoint gives no dL/dPhi and
+ * no gradient for the feature channels. Not combinable with SNERG_FLAG_PER_SAMPLE_MLP. */
+#define SNERG_FLAG_NO_MLP 8
 
 /* Pinhole camera (Sec. 4.1 r(t) = o + t d). 80 bytes, host memory.
  * Pixel (x, y) looks along R (x + 0.5 - cx) / fx, -(y + 0.5 - cy) / fy, -1) normalised,

@@ -28,6 +28,8 @@
  *   * optional alpha atlas (App. A keeps alpha in its own texture): channel 0 holds alpha
  *     codes, the sample's alpha is the trilinear code / 255, T <- T (1 - alpha), and the
  *     exit test is T < 1e-3 on a binary32 running product;
+ *   * optional ablation without the view-dependence network (the paper's performance
+ *     ablation, Sec. 6): C = C_d + T_final * background;
  *   * the backward pass is the exact adjoint of the above w.r.t. the decoded colour and
  *     feature values and the MLP weights, with density frozen (Sec. 5.5 fine-tunes the
  *     per-pixel network against an L2 image loss, Eq. 3);
@@ -89,6 +91,7 @@ typedef struct {
     int unpremultiply;     /* App. C partial un-premultiply */
     int per_sample_mlp;    /* non-deferred comparison model */
     int alpha_atlas;       /* channel 0 holds alpha codes (App. A's alpha texture) */
+    int no_mlp;            /* the performance ablation without the view-dependence network */
     float tmin32;          /* binary32(1e-3): the alpha-atlas exit threshold on T */
     float inv255_32;       /* binary32(1 / 255) */
     const double* mlp;     /* weights, for the per-sample model */
@@ -414,10 +417,11 @@ static int scene_init(OScene* S, int32_t N, int32_t B, const float* bmin, float 
     S->kappa32 = (float)(sigma_max * ((double)extent / (double)N) / 255.0);
     S->taumax32 = (float)log(1000.0);
     S->max_iter = 4 * (int64_t)N + 16;
-    if ((flags & ~7) || (flags & 3) == 3) return OR_E_INVAL;   /* un-premultiply is a deferred-model option */
+    if ((flags & ~15) || (flags & 3) == 3 || (flags & 10) == 10) return OR_E_INVAL;   /* 1 and 8 are deferred-model options */
     S->unpremultiply = (flags & 1) != 0;
     S->per_sample_mlp = (flags & 2) != 0;
     S->alpha_atlas = (flags & 4) != 0;
+    S->no_mlp = (flags & 8) != 0;
     S->tmin32 = (float)1e-3;
     S->inv255_32 = (float)(1.0 / 255.0);
     S->mlp = NULL;
@@ -460,7 +464,7 @@ int oracle_render_rays(int32_t N, int32_t B, const float* bmin, float extent, do
         for (int c = 0; c < 4; ++c) raw_v[c] = m.v[c];
         unpremultiply(&S, &m);
         double res[3] = {0.0, 0.0, 0.0};
-        if (m.active > 0) {
+        if (m.active > 0 && !S.no_mlp) {
             double x[MLP_IN];
             OMlp mm;
             mlp_input(m.cd, m.v, r.d, x);
@@ -518,11 +522,15 @@ int oracle_backward_rays(int32_t N, int32_t B, const float* bmin, float extent, 
             /* the un-premultiply scale depends on density only (frozen): a constant factor */
             const double sc = unpremultiply(&S, &m);
             double x[MLP_IN], gx[MLP_IN];
-            OMlp mm;
-            mlp_input(m.cd, m.v, r.d, x);
-            mlp_forward(mlp, x, &mm);
             const double* g = g_rgb + 3 * i;
-            mlp_backward(mlp, x, &mm, g, gl, gx);
+            if (S.no_mlp) {
+                for (int c = 0; c < MLP_IN; ++c) gx[c] = 0.0;   /* C = s C_d + T bg */
+            } else {
+                OMlp mm;
+                mlp_input(m.cd, m.v, r.d, x);
+                mlp_forward(mlp, x, &mm);
+                mlp_backward(mlp, x, &mm, g, gl, gx);
+            }
             if (!grad) continue;                  /* only dL/dPhi requested */
             double gf[7];
             for (int c = 0; c < 3; ++c) gf[c] = sc * (g[c] + gx[c]);      /* C = s C_d + residual */

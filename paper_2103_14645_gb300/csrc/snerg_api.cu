@@ -48,8 +48,11 @@ bool desc_ok(const snerg_scene_desc* d) {
     if (!(std::isfinite(d->extent) && d->extent > 0.0f)) return false;
     if (!(std::isfinite(d->sigma_max) && d->sigma_max >= 0.0f)) return false;
     if (d->max_steps < 0) return false;
-    if (d->flags & ~(SNERG_FLAG_UNPREMULTIPLY | SNERG_FLAG_PER_SAMPLE_MLP | SNERG_FLAG_ALPHA_ATLAS)) return false;
+    if (d->flags & ~(SNERG_FLAG_UNPREMULTIPLY | SNERG_FLAG_PER_SAMPLE_MLP | SNERG_FLAG_ALPHA_ATLAS |
+                     SNERG_FLAG_NO_MLP))
+        return false;
     if ((d->flags & SNERG_FLAG_UNPREMULTIPLY) && (d->flags & SNERG_FLAG_PER_SAMPLE_MLP)) return false;
+    if ((d->flags & SNERG_FLAG_NO_MLP) && (d->flags & SNERG_FLAG_PER_SAMPLE_MLP)) return false;
     return finite3(d->bmin) && finite3(d->bg);
 }
 

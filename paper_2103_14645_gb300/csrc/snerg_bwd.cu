@@ -164,11 +164,18 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
         for (int c = 0; c < 3; ++c) cd[c] *= sc;
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] *= sc;
-        stage_mlp_input(row + kRowX, cd, v, r.d);
         g[0] = __ldg(grad_rgb + 3 * i);
         g[1] = __ldg(grad_rgb + 3 * i + 1);
         g[2] = __ldg(grad_rgb + 3 * i + 2);
-        mlp_forward_backward(sW, row, g, gx);
+        if (s.flags & SNERG_FLAG_NO_MLP) {
+            // C = s C_d + T bg: nothing reaches the network, and V reaches nothing
+#pragma unroll
+            for (int c = 0; c < 7; ++c) gx[c] = 0.0f;
+            for (int k = 0; k < kRow; ++k) row[k] = 0.0f;
+        } else {
+            stage_mlp_input(row + kRowX, cd, v, r.d);
+            mlp_forward_backward(sW, row, g, gx);
+        }
     } else {
         for (int k = 0; k < kRow; ++k) row[k] = 0.0f;   // contributes nothing to the sums below
     }

@@ -762,6 +762,9 @@ __device__ __forceinline__ void finish_ray(const DevScene& s, const float* sW, f
     if (s.flags & SNERG_FLAG_PER_SAMPLE_MLP) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) res[c] = st.rgb_ps[c];
+    } else if (st.active > 0 && (s.flags & SNERG_FLAG_NO_MLP)) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res[c] = cd[c];
     } else if (st.active > 0) {
         float m[3];
         if (pw) {

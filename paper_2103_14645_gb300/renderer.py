@@ -20,6 +20,7 @@ MLP_PARAMS = 883
 FLAG_UNPREMULTIPLY = 1
 FLAG_PER_SAMPLE_MLP = 2
 FLAG_ALPHA_ATLAS = 4
+FLAG_NO_MLP = 8
 MAX_CAMERAS = 256
 AUX_CH = 8
 

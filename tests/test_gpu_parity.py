@@ -737,3 +737,25 @@ def test_row_option_errors():
     r.render(sc.cameras, None, out=out, rows=(int(sc.cameras[0]["H"]) + 5, int(sc.cameras[0]["H"]) + 9))
     torch.cuda.synchronize()
     assert (out == 7.0).all()                     # rows beyond the image: nothing written
+
+
+# --------------------------------------------------------------------------------------
+# the performance ablation without the view-dependence network
+# --------------------------------------------------------------------------------------
+
+def test_no_mlp_forward_and_backward_parity():
+    sc0 = scene("gauss64")
+    sc = synth.custom_scene(sc0.N, sc0.B, sc0.ind, sc0.atlas, sc0.sigma_max, sc0.mlp, sc0.cameras,
+                            flags=renderer.FLAG_NO_MLP)
+    g, r = gpu_render(sc, aux=True, counts=True, trace_cap=64)
+    o = oracle_all(sc, trace_cap=64)
+    assert_parity(g, o)
+    r.set_mlp(sc.mlp)
+    got = r.render(sc.cameras, None, persistent=True, tile=(8, 4), ctas_per_sm=2).cpu().numpy()
+    assert np.abs(got - o["rgb"]).max() <= TOL
+    pix, gr = _bwd_case(sc, 4096, 71)
+    ga, gm, _ = gpu_backward(sc, pix, gr)
+    ra, rm = oracle.backward_rays(sc, pix, gr)
+    assert (gm == 0).all() and (rm == 0).all()
+    assert np.abs(ga - ra).max() <= 1e-4 * np.abs(ra).max()
+    assert (ga[..., 4:] == 0).all()

@@ -64,11 +64,13 @@ def test_workspace_bytes(lib):
     neg = _desc()
     neg.max_steps = -1
     badflag = _desc()
-    badflag.flags = 8                # undefined bit
+    badflag.flags = 16               # undefined bit
+    nomlp_ps = _desc()
+    nomlp_ps.flags = 10              # no network and the per-sample network
     combo = _desc()
     combo.flags = 3                  # un-premultiply belongs to the deferred model
     for bad in [_desc(64, 6), _desc(60, 8), _desc(64, 8, extent=0.0), _desc(64, 8, sigma=float("nan")),
-                _desc(0, 8), _desc(64 * 1024, 8), _desc(8192, 4), neg, badflag, combo]:
+                _desc(0, 8), _desc(64 * 1024, 8), _desc(8192, 4), neg, badflag, combo, nomlp_ps]:
         assert lib.snerg_workspace_bytes(ctypes.byref(bad), 10) == 0
     assert lib.snerg_workspace_bytes(ctypes.byref(_desc()), -1) == 0
     assert lib.snerg_workspace_bytes(None, 1) == 0

@@ -624,3 +624,45 @@ def test_alpha_atlas_gradient_matches_central_differences():
         fp = _loss(sc, pix, target, val=vp)[0]
         fm = _loss(sc, pix, target, val=vm)[0]
         np.testing.assert_allclose(g_val[i], (fp - fm) / (2 * h), rtol=1e-5, atol=1e-8)
+
+
+# --------------------------------------------------------------------------------------
+# the performance ablation without the view-dependence network (flag 8)
+# --------------------------------------------------------------------------------------
+
+def test_no_mlp_colour_is_diffuse_plus_background():
+    """Without the network the pixel is its composited diffuse colour plus T * background,
+    whatever the weights; the composites and counts are the deferred model's."""
+    sc = synth.make_scene("gauss64")
+    pix = _pix(sc)
+    ref = oracle.render_rays(sc, pix)
+    sc8 = synth.custom_scene(sc.N, sc.B, sc.ind, sc.atlas, sc.sigma_max, sc.mlp, sc.cameras, flags=8)
+    out = oracle.render_rays(sc8, pix)
+    T = 1.0 - out["aux"][:, 7]
+    np.testing.assert_allclose(out["rgb"], out["aux"][:, :3] + T[:, None] * np.asarray(sc.bg), rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(out["aux"], ref["aux"])
+    np.testing.assert_array_equal(out["counts"], ref["counts"])
+    other = oracle.render_rays(sc8, pix, mlp=np.zeros(synth.MLP_NPARAM, np.float32))
+    np.testing.assert_array_equal(other["rgb"], out["rgb"])
+    assert np.abs(out["rgb"] - ref["rgb"]).max() > 1e-2
+
+
+def test_no_mlp_gradient_matches_central_differences():
+    sc = synth.make_scene("tiny")
+    sc = synth.custom_scene(sc.N, sc.B, sc.ind, sc.atlas, sc.sigma_max, sc.mlp, sc.cameras, flags=8)
+    pix = _pix(sc)[::2]
+    rng = np.random.default_rng(13)
+    target = rng.uniform(size=(pix.shape[0], 3))
+    val = sc.atlas.astype(np.float64) / 255.0
+    g_val, g_mlp = oracle.backward_rays(sc, pix, oracle.render_rays(sc, pix, val=val)["rgb"] - target, val=val)
+    assert (g_mlp == 0).all() and (g_val[..., 4:] == 0).all()      # features reach nothing
+    idx = np.argwhere(np.abs(g_val[..., 1:4]) > 1e-4)
+    assert idx.shape[0] > 10
+    h = 1e-6
+    for j in idx[rng.choice(idx.shape[0], 8, replace=False)]:
+        i = tuple(j[:-1]) + (j[-1] + 1,)
+        vp, vm = val.copy(), val.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd = (_loss(sc, pix, target, val=vp)[0] - _loss(sc, pix, target, val=vm)[0]) / (2 * h)
+        np.testing.assert_allclose(g_val[i], fd, rtol=1e-5, atol=1e-9)
