@@ -179,7 +179,8 @@ snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, int32_t n_ca
  *   d_rgb : float32 device image [pixels][3] through out_offset (the render's output);
  *   h_rgb : HOST float32 [pixels][3] through out_offset; page-locked memory makes the
  *           copies asynchronous, so that they overlap the rest of the render.
- * d_mlp as for snerg_render (NULL = the snerg_set_mlp weights). */
+ * d_mlp as for snerg_render (NULL = the snerg_set_mlp weights). Call it with the handle's
+ * device current (the side streams belong to that device). */
 snerg_status snerg_render_to_host(snerg_handle h, const snerg_camera* cams, int32_t n_cams, const float* d_mlp,
                                   float* d_rgb, float* h_rgb, int32_t n_bands, void* stream);
 

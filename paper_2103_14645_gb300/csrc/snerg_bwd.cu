@@ -10,6 +10,8 @@
 // the ray in forward order and needs no per-sample state. MLP weight gradients are
 // summed over the CTA's rays from activations staged in shared memory and reach global
 // memory with one atomic per parameter per CTA.
+#include <atomic>
+
 #include "snerg_internal.cuh"
 
 namespace snerg {
@@ -19,7 +21,8 @@ namespace snerg {
 // so rows of neighbouring threads fall in different banks.
 constexpr int kBwdThreads = 128;
 constexpr int kRowX = 0, kRowH1 = 34, kRowH2 = 50, kRowG1 = 66, kRowG2 = 82, kRowGZ = 98, kRow = 101;
-constexpr int kWFloats = 884;     // transposed weights (883) rounded up to a 16-byte multiple
+constexpr int kWFloats = 884;
+constexpr int kMaxDevices = 64;     // transposed weights (883) rounded up to a 16-byte multiple
 
 size_t backward_smem_bytes() { return (size_t)(kWFloats + kBwdThreads * kRow) * sizeof(float); }
 
@@ -220,12 +223,16 @@ cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_
                                  const int32_t* fwd_counts, float* grad_atlas, float* grad_mlp, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t smem = backward_smem_bytes();
-    static bool attr_set = false;     // the opt-in for > 48 KB of dynamic shared memory
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(backward_rays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    // the opt-in for > 48 KB of dynamic shared memory, once per device
+    static std::atomic<bool> attr_set[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!attr_set[dev].load()) {
+        e = cudaFuncSetAttribute(backward_rays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set[dev].store(true);
     }
     const unsigned grid = (unsigned)((n + kBwdThreads - 1) / kBwdThreads);
     backward_rays_kernel<<<grid, kBwdThreads, smem, st>>>(s, cams, n_cams, pix, n, mlp, grad_rgb, fwd_aux,
