@@ -271,7 +271,8 @@ snerg_status snerg_adam_step(float* d_param, float* d_m, float* d_v, const float
  *       distance map).
  *   d_status : nullable device int32; receives SNERG_OK or the first device-side error
  *       of this call (SNERG_E_INVAL for a bad pixel or atlas entry).
- * Limit: N / B <= 64; larger grids return SNERG_E_UNSUPPORTED.
+ * Limit: N / B <= 64; larger grids return SNERG_E_UNSUPPORTED. Of the scene flags only
+ * SNERG_FLAG_UNPREMULTIPLY is accepted (others return SNERG_E_INVAL).
  * Scratch: a status word and the block-level empty-space distance map live in one static
  * device array of 786,688 bytes that every GPU loading this library holds until the
  * process exits. The first call on each device looks up that array's device address
