@@ -4,7 +4,6 @@ flags, cameras outside and inside the grid at random poses and image sizes, slot
 the atlas. The bar is the parity bar of the other GPU tests: step counts, composited
 counts and visited voxels bit-exact, colours and composites within 1e-4, gradients within
 1e-4 of the largest oracle entry."""
-import math
 
 import numpy as np
 import pytest

@@ -202,7 +202,7 @@ def test_mlp_input_layout():
     np.testing.assert_allclose(x, np.concatenate(ref), rtol=0, atol=1e-15)
 
 
-def _brute_force_ray(scene, dense, mlp, cam, px, py, unpremultiply=False, alpha_atlas=False):
+def _brute_force_ray(scene, dense, mlp, cam, px, py, unpremultiply=False, alpha_atlas=False, no_mlp=False):
     """Definition of the march evaluated by library routines on a dense grid:
     trilinear by scipy.ndimage.map_coordinates (order 1, clamp-to-edge), transmittance
     by a running product, MLP by torch float64 linear layers. With alpha_atlas, channel 0
@@ -248,7 +248,9 @@ def _brute_force_ray(scene, dense, mlp, cam, px, py, unpremultiply=False, alpha_
         feat = feat * sc
         T = 1 - min(1.0, 1.5 * a)
     rgb = np.asarray(scene.bg) * T
-    if visited:
+    if visited and no_mlp:
+        rgb = rgb + feat[:3]
+    elif visited:
         dd = np.asarray(d, np.float64)
         pe = [feat[:3], feat[3:], dd]
         for l in range(4):
@@ -666,3 +668,52 @@ def test_no_mlp_gradient_matches_central_differences():
         vm[i] -= h
         fd = (_loss(sc, pix, target, val=vp)[0] - _loss(sc, pix, target, val=vm)[0]) / (2 * h)
         np.testing.assert_allclose(g_val[i], fd, rtol=1e-5, atol=1e-9)
+
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_brute_force_random_tiny_scenes(seed):
+    """Seeded random tiny grids (block edge 2 to 8, random occupancy, density scale, slot
+    order, placement and scene flags) and random cameras, inside the grid too: the oracle
+    equals the brute force on every ray (colours, composites, counts, visited voxels)."""
+    rng = np.random.default_rng(500 + seed)
+    B = int(rng.choice([2, 4, 8]))
+    G = int(rng.integers(2, 5))
+    N = B * G
+    ind, atl = synth.gauss_grid(N, B, float(rng.uniform(0.2, 0.8)), float(rng.choice([0.3, 1.5, 6.0])),
+                                int(rng.integers(0, 1 << 30)))
+    if atl.shape[0] > 1:
+        perm = rng.permutation(atl.shape[0])
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        ind = np.where(ind >= 0, inv[np.maximum(ind, 0)], -1).astype(np.int32)
+        atl = atl[perm]
+    flags = int(rng.choice([0, 1, 4, 5, 8]))
+    extent = float(rng.uniform(1.0, 3.0))
+    bmin = tuple(float(x) for x in rng.uniform(-2.0, 0.5, 3))
+    centre = np.asarray(bmin) + extent / 2
+    occ_blocks = np.argwhere(ind >= 0)                  # (z, y, x): look at an occupied block
+    cams = np.zeros(2, synth.CAMERA_DTYPE)
+    for i in range(2):
+        bz, by, bx = occ_blocks[rng.integers(0, occ_blocks.shape[0])]
+        tgt = np.asarray(bmin) + (np.array([bx, by, bz]) + 0.5) * B * extent / N
+        if i == 1:
+            pos = centre + rng.uniform(-0.3, 0.3, 3) * extent
+        else:
+            dvec = rng.normal(size=3)
+            pos = centre + dvec / np.linalg.norm(dvec) * extent * rng.uniform(0.9, 2.0)
+        cams[i] = synth.look_at_camera(pos, tgt, 9, 7, float(rng.uniform(30.0, 80.0)), i * 63)
+    sc = synth.custom_scene(N, B, ind, atl, 1.5 / (extent / N), synth.init_mlp(rng), cams, bmin=bmin,
+                            extent=extent, flags=flags)
+    dense = helpers.blocks_to_dense(sc)
+    pix = synth.all_pixels(cams)
+    out = oracle.render_rays(sc, pix, trace_cap=4 * N + 16)
+    assert (out["counts"][:, 1] > 0).any()
+    for i, (c, x, y) in enumerate(pix):
+        rgb, feat, steps, visited = _brute_force_ray(sc, dense, sc.mlp, cams[c], x, y, bool(flags & 1),
+                                                     bool(flags & 4), bool(flags & 8))
+        np.testing.assert_allclose(out["rgb"][i], rgb, rtol=0, atol=1e-10)
+        np.testing.assert_allclose(out["aux"][i, :7], feat, rtol=0, atol=1e-10)
+        assert out["counts"][i, 0] == steps
+        assert out["counts"][i, 1] == len(visited)
+        assert out["trace"][i, :len(visited)].tolist() == visited
