@@ -418,9 +418,47 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
     del rs, fta
     del rb, ga, gm
     out["bake"] = bake_section(args, dev, stream, flush)
+    out["orbit"] = orbit_section(args, r, sc, dev, stream, flush)
     if not args.no_large:
         out["large"] = large_section(args, dev, stream, flush)
     return out
+
+
+def orbit_section(args, r, sc, dev, stream, flush):
+    """The paper's timing protocol (App. B): the average frame time of a 150-frame camera
+    animation orbiting the scene, 800x800 at 39 deg FOV, here on the 1024^3 grid (one
+    plain launch per frame, L2 flushed before every frame)."""
+    import math
+    import torch
+    from paper_2103_14645_gb300 import synth
+    r.set_mlp(sc.mlp)
+    out = torch.empty((800 * 800, 3), dtype=torch.float32, device=dev)
+    el = math.radians(20.0)
+    cams = []
+    for i in range(150):
+        az = 2.0 * math.pi * i / 150
+        pos = synth.CAM_RADIUS * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+        cams.append(synth.look_at_camera(pos, (0.0, 0.0, 0.0), 800, 800, 39.0))
+    for c in cams[:3]:
+        r.render(np.asarray([c]), None, out=out)
+    torch.cuda.synchronize()
+    ms = []
+    for c in cams:
+        one = np.asarray([c])
+        flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r.render(one, None, out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    ms = np.asarray(ms)
+    return {"frames": 150, "ms_per_frame_mean": round(float(ms.mean()), 4),
+            "ms_per_frame_min": round(float(ms.min()), 4), "ms_per_frame_max": round(float(ms.max()), 4),
+            "frames_per_s": round(1e3 / float(ms.mean()), 1),
+            "mrays_s": round(800 * 800 / (float(ms.mean()) * 1e-3) / 1e6, 3),
+            "paper_webgl_ms_per_frame": 11.9}
 
 
 def bake_section(args, dev, stream, flush):
