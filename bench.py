@@ -187,7 +187,7 @@ def run_reference(args, ws, rank):
         oracle.render_rays(sc, samples[i % 4])
     dt = time.perf_counter() - t0
     v = n * args.steps / dt / 1e6
-    cores = os.cpu_count()
+    cores = oracle.threads()
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Mrays/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -536,11 +536,21 @@ def cpu_baseline(sc):
     from paper_2103_14645_gb300 import synth
     pix = synth.all_pixels(sc.cameras)
     oracle.render_rays(sc, pix[:1000])
+    threads = oracle.threads()
     t0 = time.perf_counter()
     oracle.render_rays(sc, pix)
     dt = time.perf_counter() - t0
-    return {"value": round(pix.shape[0] / dt / 1e6, 4), "unit": "Mrays/s", "cores": os.cpu_count(),
-            "kind": "oracle", "sample": "the full 800x800 view once (640,000 rays), FP64 C oracle with OpenMP"}
+    # one thread on every 16th ray of the view
+    oracle.set_threads(1)
+    sub = pix[::16]
+    t1 = time.perf_counter()
+    oracle.render_rays(sc, sub)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(threads)
+    return {"value": round(pix.shape[0] / dt / 1e6, 4), "unit": "Mrays/s", "cores": threads,
+            "kind": "oracle", "sample": "the full 800x800 view once (640,000 rays), FP64 C oracle with OpenMP",
+            "single_core_value": round(sub.shape[0] / dt1 / 1e6, 4),
+            "single_core_sample": f"every 16th ray of the view ({sub.shape[0]} rays), one thread"}
 
 
 def main():

@@ -66,6 +66,10 @@ def _lib():
         lib.oracle_bake_blocks.restype = None
         lib.oracle_requantize.argtypes = [P, i64, P]
         lib.oracle_requantize.restype = None
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_threads.restype = None
         _LIB = lib
     return _LIB
 
@@ -285,3 +289,13 @@ def bake_blocks(N, B, bmin, extent, sigma_max, blobs, colors, jitter, blocks, al
                               blobs.shape[0], _p(blobs), _p(colors), _p(jitter), blocks.shape[0], _p(blocks),
                               _p(amax), _p(content), _p(raw), int(bool(alpha_codes)))
     return amax, content, raw
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops use."""
+    return int(_lib().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's later parallel loops (calling thread)."""
+    _lib().oracle_set_threads(int(n))

@@ -55,6 +55,9 @@
 #pragma STDC FP_CONTRACT OFF
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -710,4 +713,23 @@ void oracle_requantize(const float* x, int64_t n, uint8_t* out) {
         const float q = floorf(fmaf(x[i], 255.0f, 0.5f));
         out[i] = q > 0.0f ? (q < 255.0f ? (uint8_t)q : 255) : 0;
     }
+}
+
+
+/* Threads the parallel loops use (the timing of the CPU baseline reports it), and a way to
+ * change it for the calling thread's later loops. */
+int oracle_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
