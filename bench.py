@@ -40,7 +40,6 @@ CSRC = os.path.join(ROOT, "paper_2103_14645_gb300", "csrc")
 
 # the sources the forward render kernels are compiled from (march core + launchers)
 RENDER_SOURCES = ("snerg_internal.cuh", "snerg_fwd.cu")
-E2E_BANDS = 4          # row bands of the end-to-end render (copy of each band overlaps the rest)
 
 
 def kernel_source_digest() -> str:
@@ -282,9 +281,9 @@ def run_ours(args, ws, rank, local):
     host_out = torch.empty((n_rays, 3), dtype=torch.float32, pin_memory=True)
 
     def e2e_step():
-        # the image in row bands on the library's side streams, each band copied to pinned
-        # host memory as soon as it is rendered; the step ends when the last band has arrived
-        r.render_to_host(cams, host_out, mlp, out=out, bands=E2E_BANDS)
+        # the kernels store the pixels straight into the pinned host buffer through the
+        # device's mapping of it (NVLink-C2C); the step ends when they are all there
+        r.render_to_host(cams, host_out, mlp)
 
     barrier()
     ms_e2e = time_steps(e2e_step, args.steps, args.warmup, stream, flush)

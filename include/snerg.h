@@ -169,16 +169,19 @@ snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, int32_t n_ca
                           const float* d_mlp, float* d_rgb, const snerg_render_opts* opts,
                           void* stream);
 
-/* Render every pixel of n_cams cameras and deliver the image to host memory, overlapping
- * the device-to-host copy with the render: the rows are split into n_bands bands
- * (1..16; the rows of every camera, by the tallest camera's height), each band is rendered
- * on one of the handle's side streams (created by the first call) after the work already
- * queued on `stream`, and copied to h_rgb as soon as it is done; `stream` then waits for
- * every band, so h_rgb is complete once `stream` is synchronised. The rays and colours are
- * those of snerg_render (plain launch).
- *   d_rgb : float32 device image [pixels][3] through out_offset (the render's output);
- *   h_rgb : HOST float32 [pixels][3] through out_offset; page-locked memory makes the
- *           copies asynchronous, so that they overlap the rest of the render.
+/* Render every pixel of n_cams cameras and deliver the image to host memory h_rgb
+ * (float32 [pixels][3] through out_offset), with the rays and colours of snerg_render
+ * (plain launch), asynchronously on `stream`; h_rgb is complete once `stream` is
+ * synchronised.
+ *   * h_rgb page-locked and mapped for the device (memory from cudaHostAlloc /
+ *     cudaMallocHost under unified addressing, e.g. PyTorch's pinned tensors): the kernels
+ *     store the pixels straight into it through the device's mapping (NVLink-C2C on a Grace
+ *     host), so no copy follows the render; d_rgb and n_bands are not used (d_rgb may be
+ *     NULL).
+ *   * otherwise: the rows are split into n_bands bands (1..16, by the tallest camera), each
+ *     rendered into d_rgb (float32 device image, required) on one of the handle's side
+ *     streams (created by the first call) after the work already queued on `stream`, and
+ *     copied to h_rgb as soon as it is done; `stream` waits for every band.
  * d_mlp as for snerg_render (NULL = the snerg_set_mlp weights). Call it with the handle's
  * device current (the side streams belong to that device). */
 snerg_status snerg_render_to_host(snerg_handle h, const snerg_camera* cams, int32_t n_cams, const float* d_mlp,

@@ -445,9 +445,25 @@ extern "C" snerg_status snerg_render_to_host(snerg_handle h, const snerg_camera*
         Hmax = std::max(Hmax, cams[i].H);
     }
     if (pixels == 0) return SNERG_OK;
-    if (!d_rgb || !h_rgb || (!d_mlp && !h->has_w)) return SNERG_E_INVAL;
+    if (!h_rgb || (!d_mlp && !h->has_w)) return SNERG_E_INVAL;
     const MlpWeights* pw = d_mlp ? nullptr : &h->host_w;
     cudaStream_t st = (cudaStream_t)stream;
+    const DebugOut dbg{nullptr, nullptr, nullptr, 0};
+    // page-locked host memory mapped for the device: the kernels store the pixels straight
+    // into it (over NVLink-C2C on a Grace host), so the frame needs no separate copy
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, h_rgb) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+        float* mapped = (float*)pa.devicePointer;
+        for (int i = 0; i < n_cams; ++i) {
+            if (cams[i].W == 0 || cams[i].H == 0) continue;
+            if (launch_render_image(h->ds, cams[i], d_mlp, pw, mapped, dbg, st, 0, cams[i].H) != cudaSuccess)
+                return SNERG_E_CUDA;
+            h->launches++;
+        }
+        return SNERG_OK;
+    }
+    cudaGetLastError();                  // an unregistered pointer is not an error here
+    if (!d_rgb) return SNERG_E_INVAL;
     cudaError_t e = cudaSuccess;
     if (!h->band_fork) e = cudaEventCreateWithFlags(&h->band_fork, cudaEventDisableTiming);
     while (e == cudaSuccess && (int)h->band_streams.size() < n_bands) {
@@ -459,7 +475,6 @@ extern "C" snerg_status snerg_render_to_host(snerg_handle h, const snerg_camera*
         if (e == cudaSuccess) h->band_done.push_back(d);
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->band_fork, st);
-    const DebugOut dbg{nullptr, nullptr, nullptr, 0};
     n_bands = std::min(n_bands, Hmax);
     for (int b = 0; b < n_bands && e == cudaSuccess; ++b) {
         const int y0 = (int)((int64_t)Hmax * b / n_bands), y1 = (int)((int64_t)Hmax * (b + 1) / n_bands);

@@ -275,23 +275,23 @@ class Renderer:
 
     def render_to_host(self, cams, host_out: torch.Tensor, mlp: torch.Tensor | None = None,
                        out: torch.Tensor | None = None, bands: int = 4):
-        """Render the cameras into pinned host memory host_out [pixels, 3] with
-        snerg_render_to_host: `bands` row bands rendered on the library's side streams, each
-        copied out as soon as it is done, overlapping the rest of the render. Enqueued after
-        the current stream's work; host_out is complete once the current stream is
-        synchronised. `out` is the device image (allocated if None)."""
+        """Render the cameras into host memory host_out [pixels, 3] (float32, contiguous) with
+        snerg_render_to_host. Pinned host_out: the kernels write the pixels straight into it
+        (no copy after the render). Pageable host_out: `bands` row bands rendered into the
+        device image `out` (allocated if None) on the library's side streams, each copied out
+        as soon as it is done. Enqueued after the current stream's work; host_out is complete
+        once the current stream is synchronised."""
         c = _cams(cams)
-        if host_out.device.type != "cpu" or not host_out.is_pinned() or host_out.dtype != torch.float32 \
-                or not host_out.is_contiguous():
-            raise ValueError("host_out must be a contiguous pinned float32 CPU tensor")
+        if host_out.device.type != "cpu" or host_out.dtype != torch.float32 or not host_out.is_contiguous():
+            raise ValueError("host_out must be a contiguous float32 CPU tensor")
         if mlp is not None:
             _require_cuda(mlp, "mlp", torch.float32)
         n_pix = int(max((int(x["out_offset"]) + int(x["W"]) * int(x["H"]) for x in c), default=0))
         if host_out.numel() < 3 * n_pix:
             raise ValueError("host_out is too small")
-        if out is None:
+        if out is None and not host_out.is_pinned():
             out = torch.empty((n_pix, 3), dtype=torch.float32, device=self.device)
-        else:
+        elif out is not None:
             _require_cuda(out, "out", torch.float32)
             if out.numel() < 3 * n_pix:
                 raise ValueError("out is too small")

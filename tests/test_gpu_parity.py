@@ -701,19 +701,24 @@ def test_row_bands_reproduce_the_full_render(name):
 
 
 def test_render_to_host_matches_the_device_render():
-    """The banded render with per-band copies into pinned memory returns the device image
-    exactly, for one camera and for a batch of ragged cameras, with 1, 3 and 8 bands."""
+    """Into pinned memory the kernels write the pixels directly; into pageable memory the
+    frame goes in row bands (1, 3, 8, 16) with a copy per band. Both return the device image
+    exactly, for one camera and for a batch of ragged cameras."""
     sc = scene("gauss64")
     r = renderer.Renderer.from_scene(sc, DEV)
     r.set_mlp(sc.mlp)
     cams = synth.orbit_cameras(np.random.default_rng(12), [(37, 23), (64, 64), (5, 70)], synth.CAM_RADIUS)
     for cs in (sc.cameras, cams):
         ref = r.render(cs, None).cpu()
+        host = torch.full((ref.shape[0], 3), float("nan"), dtype=torch.float32, pin_memory=True)
+        r.render_to_host(cs, host)
+        torch.cuda.current_stream(DEV).synchronize()
+        assert torch.equal(host, ref)
         for bands in (1, 3, 8, 16):
-            host = torch.full((ref.shape[0], 3), float("nan"), dtype=torch.float32, pin_memory=True)
-            r.render_to_host(cs, host, bands=bands)
+            page = torch.full((ref.shape[0], 3), float("nan"), dtype=torch.float32)
+            r.render_to_host(cs, page, bands=bands)
             torch.cuda.current_stream(DEV).synchronize()
-            assert torch.equal(host, ref), bands
+            assert torch.equal(page, ref), bands
     r.check_status()
 
 
