@@ -161,7 +161,9 @@ snerg_status snerg_set_mlp(snerg_handle h, const float* mlp);
  *   d_mlp  : float32 [SNERG_MLP_PARAMS] view-dependence MLP weights in device memory,
  *            or NULL to use the weights stored with snerg_set_mlp (SNERG_E_INVAL if
  *            none were stored).
- *   d_rgb  : float32 output [total pixels][3] addressed through out_offset.
+ *   d_rgb  : float32 output [total pixels][3] addressed through out_offset; device memory,
+ *            or page-locked host memory mapped for the device (the kernels then store the
+ *            pixels into host memory directly, see snerg_render_to_host).
  *   opts   : nullable. Debug outputs (aux, counts, trace) use the plain launch.
  * The colour is C = C_d + sigmoid(MLP(C_d, V, PE(d))) + T bg if any sample was
  * composited, else T bg (App. A evaluates the MLP only where alpha > 0). */
