@@ -369,7 +369,13 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
     ms_p = time_steps(lambda: r.render(cams, mlp, out=buf), reps, 2, stream, flush)
     barrier()
     tw, th, c = r.persistent_config()
+    # end to end: the same persistent launch storing the 64 images straight into pinned
+    # host memory (487 MB per batch through the device's mapping)
+    host = torch.empty((n_pix, 3), dtype=torch.float32, pin_memory=True)
+    ms_h = time_steps(lambda: r.render(cams, mlp, out=host, persistent=True), reps, 2, stream, flush)
+    del host
     out["batched"] = {"cameras": int(len(cams)), "rays": n_pix,
+                      "persistent_to_host_mrays_s": round(n_pix / (np.mean(ms_h) * 1e-3) / 1e6, 3),
                       "persistent_mrays_s": round(n_pix / (np.mean(ms_b) * 1e-3) / 1e6, 3),
                       "plain_mrays_s": round(n_pix / (np.mean(ms_p) * 1e-3) / 1e6, 3),
                       "ratio": round(float(np.mean(ms_p) / np.mean(ms_b)), 4),

@@ -248,7 +248,8 @@ class Renderer:
 
     def render(self, cams, mlp: torch.Tensor | None, out: torch.Tensor | None = None, aux=False, counts=False,
                trace_cap: int = 0, persistent=False, tile=None, ctas_per_sm: int = 0, rows=None):
-        """Render every pixel of the cameras into out [pixels, 3] (packed by out_offset).
+        """Render every pixel of the cameras into out [pixels, 3] (packed by out_offset), a
+        device tensor or a pinned host tensor (written by the kernels through the mapping).
         mlp: device weights, or None for the weights stored with set_mlp.
         rows: (begin, end) renders only those image rows of every camera.
         Returns out, or a dict with 'rgb' and the requested debug outputs."""
@@ -259,7 +260,12 @@ class Renderer:
         if out is None:
             out = torch.empty((n_pix, 3), dtype=torch.float32, device=self.device)
         else:
-            _require_cuda(out, "out", torch.float32)
+            if out.device.type == "cpu":
+                # pinned host memory is mapped for the device: the kernels store into it
+                if not out.is_pinned() or out.dtype != torch.float32 or not out.is_contiguous():
+                    raise ValueError("a host out must be a contiguous pinned float32 tensor")
+            else:
+                _require_cuda(out, "out", torch.float32)
             if out.numel() < 3 * n_pix:
                 raise ValueError("out is too small")
         o, extra = self._opts(n_pix, aux, counts, trace_cap, persistent, tile, ctas_per_sm)

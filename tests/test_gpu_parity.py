@@ -783,3 +783,21 @@ def test_batched_64_cameras_paper_scale_sampled():
     r.check_status()
     np.testing.assert_array_equal(got["counts"].cpu().numpy()[:, :2], o["counts"])
     assert (o["counts"][:, 1] > 0).mean() > 0.05
+
+
+def test_render_into_pinned_host_memory_all_paths():
+    """The plain and the persistent launches store into a pinned host tensor through the
+    device's mapping and give the device render exactly."""
+    sc = scene("gauss64")
+    r = renderer.Renderer.from_scene(sc, DEV)
+    r.set_mlp(sc.mlp)
+    cams = synth.orbit_cameras(np.random.default_rng(13), [(37, 23), (64, 64), (5, 70), (80, 3)], synth.CAM_RADIUS)
+    ref = r.render(cams, None).cpu()
+    for persistent in (False, True):
+        host = torch.full(ref.shape, float("nan"), dtype=torch.float32, pin_memory=True)
+        r.render(cams, None, out=host, persistent=persistent)
+        torch.cuda.current_stream(DEV).synchronize()
+        assert torch.equal(host, ref), persistent
+    with pytest.raises(ValueError):
+        r.render(cams, None, out=torch.empty(ref.shape))          # pageable host memory
+    r.check_status()
