@@ -400,13 +400,22 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
         f = rb.render_rays(wsc.cameras, pix, wm, out=c, aux=True, counts=True)
         rb.backward(wsc.cameras, pix, wm, c - tgt, ga, gm, fwd_aux=f["aux"], fwd_counts=f["counts"])
 
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def fused():
+        # render, L2 loss and adjoint of every ray in one launch (snerg_train_rays)
+        rb.train_rays(wsc.cameras, pix, wm, tgt, ga, gm, loss=loss, out=c)
+
     ms_f = time_steps(fwd, reps, 2, stream, flush)
     ms_fb = time_steps(fwd_bwd, reps, 2, stream, flush)
+    ms_tr = time_steps(fused, reps, 2, stream, flush)
     n = pix.shape[0]
     out["fwd_bwd"] = {"workload": f"bwd512: {wsc.N}^3 grid, {wsc.occupancy * 100:.1f}% occupied, {n} rays over 8 views",
                       "fwd_mrays_s": round(n / (np.mean(ms_f) * 1e-3) / 1e6, 3),
                       "fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3),
-                      "ms_fwd": round(float(np.mean(ms_f)), 4), "ms_fwd_bwd": round(float(np.mean(ms_fb)), 4)}
+                      "fused_train_mrays_s": round(n / (np.mean(ms_tr) * 1e-3) / 1e6, 3),
+                      "ms_fwd": round(float(np.mean(ms_f)), 4), "ms_fwd_bwd": round(float(np.mean(ms_fb)), 4),
+                      "ms_fused_train": round(float(np.mean(ms_tr)), 4)}
     # fine-tuning steps (Sec. 5.5): render -> L2 loss -> adjoint -> Adam, all in the library
     ft = renderer.FineTuner(rb, wsc.mlp)
     ms_ft = time_steps(lambda: ft.step(wsc.cameras, pix, tgt), reps, 2, stream, flush)
@@ -522,8 +531,11 @@ def large_section(args, dev, stream, flush):
         f = r.render_rays(sc.cameras, pix, mlp, out=c, aux=True, counts=True)
         r.backward(sc.cameras, pix, mlp, c - tgt, ga, gm, fwd_aux=f["aux"], fwd_counts=f["counts"])
 
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
     ms_f = time_steps(fwd, reps, 2, stream, flush)
     ms_fb = time_steps(fwd_bwd, reps, 2, stream, flush)
+    ms_tr = time_steps(lambda: r.train_rays(sc.cameras, pix, mlp, tgt, ga, gm, loss=loss, out=c), reps, 2, stream,
+                       flush)
     r.check_status()
     peak = float(measured_peaks()[0]["hbm_gbs"])
     t_b = float(np.mean(ms_b))
@@ -533,7 +545,8 @@ def large_section(args, dev, stream, flush):
             "batched_fwd_ms": round(t_b, 3),
             "batched_fwd_hbm_frac": round(alg / (t_b * 1e-3) / 1e9 / peak, 4),
             "rays_fwd_mrays_s": round(n / (np.mean(ms_f) * 1e-3) / 1e6, 3),
-            "rays_fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3)}
+            "rays_fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3),
+            "rays_fused_train_mrays_s": round(n / (np.mean(ms_tr) * 1e-3) / 1e6, 3)}
 
 
 def cpu_baseline(sc):

@@ -250,6 +250,19 @@ snerg_status snerg_grad_blocks_scatter(const float* d_packed, const int32_t* d_l
  * render the new codes. */
 snerg_status snerg_requantize_atlas(snerg_handle h, const float* d_values, uint8_t* d_atlas_out, void* stream);
 
+/* One fine-tuning step's render, loss and adjoint for a ray list in a single launch (Sec.
+ * 5.5, Eq. 3): each ray is marched and shaded as by snerg_render_rays, its L2 loss
+ * |C - C*|^2 is ADDED to *d_loss (caller zeroes; nullable), dL/dC = 2 (C - C*) is taken in
+ * the kernel, and the adjoint ACCUMULATES into d_grad_atlas / d_grad_mlp exactly as
+ * snerg_render_backward does for that upstream gradient (either nullable).
+ *   d_target : float32 [n][3], the observed colours C*;
+ *   d_rgb    : nullable float32 [n][3], receives C.
+ * The same result as snerg_render_rays + snerg_l2_loss + snerg_render_backward, without
+ * the per-ray state between them. d_mlp must be device weights. */
+snerg_status snerg_train_rays(snerg_handle h, const snerg_camera* cams, int32_t n_cams, const int32_t* d_pix,
+                              int64_t n, const float* d_mlp, const float* d_target, float* d_rgb, float* d_loss,
+                              float* d_grad_atlas, float* d_grad_mlp, void* stream);
+
 /* Photometric loss of Eq. 3 over n rays: *d_loss += sum |C - C*|^2 (ACCUMULATED, caller
  * zeroes; nullable), d_grad [n][3] = 2 (C - C*) (nullable). d_rgb, d_target: [n][3]. */
 snerg_status snerg_l2_loss(const float* d_rgb, const float* d_target, int64_t n, float* d_grad,

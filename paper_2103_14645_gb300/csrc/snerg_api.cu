@@ -547,6 +547,26 @@ extern "C" snerg_status snerg_render_backward(snerg_handle h, const snerg_camera
     return SNERG_OK;
 }
 
+extern "C" snerg_status snerg_train_rays(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
+                                         const int32_t* d_pix, int64_t n, const float* d_mlp, const float* d_target,
+                                         float* d_rgb, float* d_loss, float* d_grad_atlas, float* d_grad_mlp,
+                                         void* stream) {
+    if (!h || n < 0) return SNERG_E_INVAL;
+    if (h->desc.flags & SNERG_FLAG_PER_SAMPLE_MLP) return SNERG_E_UNSUPPORTED;
+    CamTable* t = new (std::nothrow) CamTable;
+    if (!t) return SNERG_E_NOMEM;
+    if (!make_table(cams, n_cams, t)) { delete t; return SNERG_E_INVAL; }
+    if (n == 0) { delete t; return SNERG_OK; }
+    if (!d_pix || !d_mlp || !d_target) { delete t; return SNERG_E_INVAL; }
+    if (d_grad_atlas && ((uintptr_t)d_grad_atlas & 15u)) { delete t; return SNERG_E_INVAL; }
+    cudaError_t e = launch_train_rays(h->ds, *t, n_cams, d_pix, n, d_mlp, d_target, d_rgb, d_loss, d_grad_atlas,
+                                      d_grad_mlp, (cudaStream_t)stream);
+    delete t;
+    if (e != cudaSuccess) return SNERG_E_CUDA;
+    h->launches++;
+    return SNERG_OK;
+}
+
 extern "C" snerg_status snerg_last_status(snerg_handle h, void* stream) {
     if (!h) return SNERG_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;

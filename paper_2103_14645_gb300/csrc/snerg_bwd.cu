@@ -26,9 +26,8 @@ constexpr int kMaxDevices = 64;     // transposed weights (883) rounded up to a 
 
 size_t backward_smem_bytes() { return (size_t)(kWFloats + kBwdThreads * kRow) * sizeof(float); }
 
-// MLP forward keeping activations, then its adjoint for dL/dres = g; writes h1, h2, g1,
-// g2, gz into the row and returns dL/dx for the 7 composited inputs (C_d, V).
-__device__ __forceinline__ void mlp_forward_backward(const float* sW, float* row, const float g[3], float gx[7]) {
+// MLP forward keeping the activations h1, h2 in the row; returns the sigmoid residual.
+__device__ __forceinline__ void mlp_forward_rows(const float* sW, float* row, float res[3]) {
     float h[16];
     load16(h, sW + kOffB1);
 #pragma unroll 2
@@ -47,14 +46,23 @@ __device__ __forceinline__ void mlp_forward_backward(const float* sW, float* row
         h2[o] = fmaxf(h2[o], 0.0f);
         row[kRowH2 + o] = h2[o];
     }
-    float gz[3];
 #pragma unroll
     for (int o = 0; o < kMlpOut; ++o) {
         float acc = sW[kOffB3 + o];
 #pragma unroll
         for (int i = 0; i < kMlpH; ++i) acc = fmaf(sW[kOffW3 + o * kMlpH + i], h2[i], acc);
-        const float r = 1.0f / (1.0f + expf(-acc));
-        gz[o] = g[o] * r * (1.0f - r);                 // sigmoid'
+        res[o] = 1.0f / (1.0f + expf(-acc));
+    }
+}
+
+// Adjoint of the MLP for dL/dres = g, from the activations in the row and the residual:
+// writes gz, g2, g1 into the row and returns dL/dx for the 7 composited inputs (C_d, V).
+__device__ __forceinline__ void mlp_backward_rows(const float* sW, float* row, const float res[3], const float g[3],
+                                                  float gx[7]) {
+    float gz[3];
+#pragma unroll
+    for (int o = 0; o < kMlpOut; ++o) {
+        gz[o] = g[o] * res[o] * (1.0f - res[o]);       // sigmoid'
         row[kRowGZ + o] = gz[o];
     }
     float g2[16];
@@ -63,7 +71,7 @@ __device__ __forceinline__ void mlp_forward_backward(const float* sW, float* row
         float acc = 0.0f;
 #pragma unroll
         for (int o = 0; o < kMlpOut; ++o) acc = fmaf(sW[kOffW3 + o * kMlpH + k], gz[o], acc);
-        g2[k] = h2[k] > 0.0f ? acc : 0.0f;           // ReLU'
+        g2[k] = row[kRowH2 + k] > 0.0f ? acc : 0.0f;  // ReLU'
         row[kRowG2 + k] = g2[k];
     }
     // g1 = W2^T g2 masked by ReLU', one hidden unit at a time (rolled: keeps the weight
@@ -101,15 +109,30 @@ __device__ __forceinline__ void mlp_forward_backward(const float* sW, float* row
     }
 }
 
+// MLP forward keeping activations, then its adjoint for dL/dres = g; writes h1, h2, g1,
+// g2, gz into the row and returns dL/dx for the 7 composited inputs (C_d, V).
+__device__ __forceinline__ void mlp_forward_backward(const float* sW, float* row, const float g[3], float gx[7]) {
+    float res[3];
+    mlp_forward_rows(sW, row, res);
+    mlp_backward_rows(sW, row, res, g, gx);
+}
+
 // fwd_aux / fwd_counts (nullable, both or neither): the forward's per-ray outputs
 // (C_d, V, opacity; steps, composited samples, indirection reads, first composited
 // lattice index). With them the kernel skips its own first march.
+// TRAIN: one fine-tuning step for the ray in one pass (Sec. 5.5, Eq. 3): the march and the
+// MLP give C, the L2 loss |C - C*|^2 is accumulated into *loss, dL/dC = 2 (C - C*) is taken
+// in the kernel, and the adjoint follows as for a given upstream gradient; C goes to
+// rgb_out (nullable). grad_rgb, fwd_aux and fwd_counts are not used.
+template <bool TRAIN>
 __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     const DevScene s, const __grid_constant__ CamTable cams, int32_t n_cams, const int32_t* __restrict__ pix,
     int64_t n, const float* __restrict__ mlp, const float* __restrict__ grad_rgb,
-    const float* __restrict__ fwd_aux, const int32_t* __restrict__ fwd_counts, float* __restrict__ grad_atlas,
+    const float* __restrict__ fwd_aux, const int32_t* __restrict__ fwd_counts, const float* __restrict__ target,
+    float* __restrict__ rgb_out, float* __restrict__ loss, float* __restrict__ grad_atlas,
     float* __restrict__ grad_mlp) {
     extern __shared__ __align__(16) float smem[];
+    __shared__ float s_loss[kBwdThreads / 32];
     float* sW = smem;
     float* rows = smem + kWFloats;
     load_mlp_smem_t(sW, mlp);
@@ -122,6 +145,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     r.d[0] = r.d[1] = r.d[2] = 0.0f;
     MarchState st;
     st.active = 0;
+    st.T = 1.0f;
     int k_first = 0;
     if (i < n) {
         const int ci = __ldg(pix + 3 * i), px = __ldg(pix + 3 * i + 1), py = __ldg(pix + 3 * i + 2);
@@ -129,7 +153,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
             r = make_ray(s, cams.c[ci], px, py);
         else
             atomicCAS(s.status, 0, (int)SNERG_E_INVAL);
-        if (fwd_aux) {
+        if (!TRAIN && fwd_aux) {
             // the forward's per-ray state: C_d, V (decoded) and the first composited index
             st.active = r.hit ? __ldg(fwd_counts + 4 * i + 1) : 0;
             k_first = __ldg(fwd_counts + 4 * i + 3);
@@ -144,11 +168,12 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     float g[3] = {0.0f, 0.0f, 0.0f};
     float gx[7];
     float sc = 1.0f;
+    float l2 = 0.0f;                 // TRAIN: this ray's |C - C*|^2
     if (active) {
         const float inv255 = 1.0f / 255.0f;
         float cd[3], v[4];
         float T;
-        if (fwd_aux) {
+        if (!TRAIN && fwd_aux) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) cd[c] = __ldg(fwd_aux + kAuxCh * i + c);
 #pragma unroll
@@ -167,22 +192,63 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
         for (int c = 0; c < 3; ++c) cd[c] *= sc;
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] *= sc;
-        g[0] = __ldg(grad_rgb + 3 * i);
-        g[1] = __ldg(grad_rgb + 3 * i + 1);
-        g[2] = __ldg(grad_rgb + 3 * i + 2);
-        if (s.flags & SNERG_FLAG_NO_MLP) {
+        const bool no_mlp = (s.flags & SNERG_FLAG_NO_MLP) != 0;
+        float res[3] = {0.0f, 0.0f, 0.0f};
+        if (!no_mlp) {
+            stage_mlp_input(row + kRowX, cd, v, r.d);
+            if (TRAIN) mlp_forward_rows(sW, row, res);
+        }
+        if (TRAIN) {
+            // C = s C_d + residual + T' bg (finish_ray's arithmetic), dL/dC = 2 (C - C*)
+            const float Tb = (s.flags & SNERG_FLAG_UNPREMULTIPLY) ? 1.0f - (1.0f - T) * sc : T;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float C = cd[c] + res[c] + Tb * s.bg[c];
+                const float d = C - __ldg(target + 3 * i + c);
+                if (rgb_out) rgb_out[3 * i + c] = C;
+                g[c] = 2.0f * d;
+                l2 = fmaf(d, d, l2);
+            }
+        } else {
+            g[0] = __ldg(grad_rgb + 3 * i);
+            g[1] = __ldg(grad_rgb + 3 * i + 1);
+            g[2] = __ldg(grad_rgb + 3 * i + 2);
+        }
+        if (no_mlp) {
             // C = s C_d + T bg: nothing reaches the network, and V reaches nothing
 #pragma unroll
             for (int c = 0; c < 7; ++c) gx[c] = 0.0f;
             for (int k = 0; k < kRow; ++k) row[k] = 0.0f;
+        } else if (TRAIN) {
+            mlp_backward_rows(sW, row, res, g, gx);
         } else {
-            stage_mlp_input(row + kRowX, cd, v, r.d);
             mlp_forward_backward(sW, row, g, gx);
         }
     } else {
         for (int k = 0; k < kRow; ++k) row[k] = 0.0f;   // contributes nothing to the sums below
+        if (TRAIN && i < n) {
+            // nothing composited: C = T bg (T = 1 for a ray that composited nothing)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float C = st.T * s.bg[c];
+                const float d = C - __ldg(target + 3 * i + c);
+                if (rgb_out) rgb_out[3 * i + c] = C;
+                l2 = fmaf(d, d, l2);
+            }
+        }
+    }
+    if (TRAIN && loss) {
+        float v = l2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = v;
     }
     __syncthreads();
+    if (TRAIN && loss && threadIdx.x == 0) {
+        float v = 0.0f;
+        for (int w = 0; w < kBwdThreads / 32; ++w) v += s_loss[w];
+        atomicAdd(loss, v);
+    }
     // dL/dPhi: per parameter, a dot product over the CTA's rays (one global atomic per
     // parameter per CTA): W1 <- g1 (x) x, W2 <- g2 (x) h1, W3 <- gz (x) h2, biases <- g.
     if (grad_mlp) {
@@ -218,9 +284,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     }
 }
 
-cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
-                                 int64_t n, const float* mlp, const float* grad_rgb, const float* fwd_aux,
-                                 const int32_t* fwd_counts, float* grad_atlas, float* grad_mlp, cudaStream_t st) {
+template <bool TRAIN>
+static cudaError_t backward_launch(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
+                                   int64_t n, const float* mlp, const float* grad_rgb, const float* fwd_aux,
+                                   const int32_t* fwd_counts, const float* target, float* rgb_out, float* loss,
+                                   float* grad_atlas, float* grad_mlp, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t smem = backward_smem_bytes();
     // the opt-in for > 48 KB of dynamic shared memory, once per device
@@ -230,14 +298,29 @@ cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     if (!attr_set[dev].load()) {
-        e = cudaFuncSetAttribute(backward_rays_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(backward_rays_kernel<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set[dev].store(true);
     }
     const unsigned grid = (unsigned)((n + kBwdThreads - 1) / kBwdThreads);
-    backward_rays_kernel<<<grid, kBwdThreads, smem, st>>>(s, cams, n_cams, pix, n, mlp, grad_rgb, fwd_aux,
-                                                          fwd_counts, grad_atlas, grad_mlp);
+    backward_rays_kernel<TRAIN><<<grid, kBwdThreads, smem, st>>>(s, cams, n_cams, pix, n, mlp, grad_rgb, fwd_aux,
+                                                                 fwd_counts, target, rgb_out, loss, grad_atlas,
+                                                                 grad_mlp);
     return cudaGetLastError();
+}
+
+cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
+                                 int64_t n, const float* mlp, const float* grad_rgb, const float* fwd_aux,
+                                 const int32_t* fwd_counts, float* grad_atlas, float* grad_mlp, cudaStream_t st) {
+    return backward_launch<false>(s, cams, n_cams, pix, n, mlp, grad_rgb, fwd_aux, fwd_counts, nullptr, nullptr,
+                                  nullptr, grad_atlas, grad_mlp, st);
+}
+
+cudaError_t launch_train_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
+                              const float* mlp, const float* target, float* rgb_out, float* loss, float* grad_atlas,
+                              float* grad_mlp, cudaStream_t st) {
+    return backward_launch<true>(s, cams, n_cams, pix, n, mlp, nullptr, nullptr, nullptr, target, rgb_out, loss,
+                                 grad_atlas, grad_mlp, st);
 }
 
 }  // namespace snerg

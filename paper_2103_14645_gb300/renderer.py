@@ -32,7 +32,7 @@ EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_rend
             "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc",
             "snerg_set_mlp", "snerg_l2_loss", "snerg_adam_step", "snerg_bake_workspace_bytes", "snerg_bake",
             "snerg_requantize_atlas", "snerg_grad_blocks_touched", "snerg_grad_blocks_gather",
-            "snerg_grad_blocks_scatter", "snerg_render_to_host"]
+            "snerg_grad_blocks_scatter", "snerg_render_to_host", "snerg_train_rays"]
 MAX_BAKE_BLOBS = 64
 
 
@@ -103,6 +103,8 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_set_mlp.restype = ctypes.c_int
     lib.snerg_render_rays_noalloc.argtypes = [P, P, P, i64, P, i32, P, i64, P, P, P, P]
     lib.snerg_render_rays_noalloc.restype = ctypes.c_int
+    lib.snerg_train_rays.argtypes = [P, P, i32, P, i64, P, P, P, P, P, P, P]
+    lib.snerg_train_rays.restype = ctypes.c_int
     lib.snerg_render_to_host.argtypes = [P, P, i32, P, P, P, i32, P]
     lib.snerg_render_to_host.restype = ctypes.c_int
     lib.snerg_grad_blocks_touched.argtypes = [P, i64, i32, P, P]
@@ -352,6 +354,33 @@ class Renderer:
         _check(code, "snerg_render_backward")
 
 
+
+def _train_rays(self, cams, pix: torch.Tensor, mlp: torch.Tensor, target: torch.Tensor,
+                grad_atlas: torch.Tensor | None, grad_mlp: torch.Tensor | None,
+                loss: torch.Tensor | None = None, out: torch.Tensor | None = None):
+    """One fine-tuning step's render, L2 loss (added to `loss`) and adjoint (accumulated
+    into grad_atlas / grad_mlp) for the rays pix [n,3] with observed colours target [n,3],
+    in one launch (snerg_train_rays); C goes to `out` when given."""
+    c = _cams(cams)
+    _require_cuda(pix, "pix", torch.int32)
+    _require_cuda(mlp, "mlp", torch.float32)
+    _require_cuda(target, "target", torch.float32)
+    n = int(pix.shape[0])
+    if target.numel() != 3 * n:
+        raise ValueError("target must be [n, 3]")
+    for name, t in (("grad_atlas", grad_atlas), ("grad_mlp", grad_mlp), ("loss", loss), ("out", out)):
+        if t is not None:
+            _require_cuda(t, name, torch.float32)
+    if grad_atlas is not None and grad_atlas.numel() != self.nb * self.B ** 3 * 8:
+        raise ValueError("grad_atlas must have the atlas shape")
+    code = self.lib.snerg_train_rays(self.handle, c.ctypes.data, c.shape[0], _ptr(pix), n, _ptr(mlp), _ptr(target),
+                                     _ptr(out), _ptr(loss), _ptr(grad_atlas), _ptr(grad_mlp), _stream(self.device))
+    _check(code, "snerg_train_rays")
+
+
+Renderer.train_rays = _train_rays
+
+
 class SnergRenderFn(torch.autograd.Function):
     """C(rays) with gradients to the MLP weights and to the decoded atlas values.
 
@@ -462,8 +491,9 @@ def allreduce_gradients(grad_mlp: torch.Tensor, grad_atlas: torch.Tensor | None 
 class FineTuner:
     """Fine-tunes the view-dependence MLP of a baked grid against observed pixels with
     Adam and the L2 loss, as the paper does after baking (Sec. 5.5: Adam, learning rate
-    3e-4). One step = render_rays (keeping per-ray state) -> loss and dL/dC -> backward
-    (dL/dPhi) -> Adam, all in the library's kernels.
+    3e-4). One step = the rays' render, L2 loss and adjoint (one launch of snerg_train_rays
+    while the batch fits in one wave of the adjoint kernel; render_rays -> l2_loss ->
+    backward for larger batches) -> Adam, all in the library's kernels.
 
     With `atlas` (the scene's uint8 atlas [nb,B,B,B,8]) and `atlas_lr`, the baked colours
     and features are fine-tuned too: an FP32 shadow copy (q / 255) takes Adam steps on the
@@ -486,6 +516,8 @@ class FineTuner:
         self.loss = torch.zeros(1, dtype=torch.float32, device=renderer.device)
         self.lr, self.betas, self.eps = lr, betas, eps
         self.steps = 0
+        # one wave of the adjoint kernel: 4 CTAs of 128 rays per SM
+        self.fused_rays = 4 * 128 * torch.cuda.get_device_properties(renderer.device).multi_processor_count
         self.atlas_lr = atlas_lr
         self.shadow = None
         if atlas_lr is not None:
@@ -501,16 +533,22 @@ class FineTuner:
     def step(self, cams, pix: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
         """One Adam step on rays pix [n,3] with observed colours target [n,3]; returns the
         loss before the step (a device tensor [1])."""
-        fwd = self.r.render_rays(cams, pix, self.mlp, aux=True, counts=True)
-        g = torch.empty_like(fwd["rgb"])
         self.loss.zero_()
         self.grad.zero_()
-        l2_loss(fwd["rgb"], target, g, self.loss)
         ga = None
         if self.shadow is not None:
             self.grad_atlas.zero_()
             ga = self.grad_atlas
-        self.r.backward(cams, pix, self.mlp, g, ga, self.grad, fwd_aux=fwd["aux"], fwd_counts=fwd["counts"])
+        if pix.shape[0] <= self.fused_rays:
+            # render, loss and adjoint of every ray in one launch: the batch fits in one wave
+            # of the adjoint kernel, so one launch tail replaces two
+            self.r.train_rays(cams, pix, self.mlp, target, ga, self.grad, loss=self.loss)
+        else:
+            # larger batches: the forward at its own (higher) occupancy, keeping per-ray state
+            fwd = self.r.render_rays(cams, pix, self.mlp, aux=True, counts=True)
+            g = torch.empty_like(fwd["rgb"])
+            l2_loss(fwd["rgb"], target, g, self.loss)
+            self.r.backward(cams, pix, self.mlp, g, ga, self.grad, fwd_aux=fwd["aux"], fwd_counts=fwd["counts"])
         if _data_parallel(self.group):
             allreduce_gradients(self.grad, ga, self.group)
         self.steps += 1

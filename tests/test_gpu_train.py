@@ -181,3 +181,67 @@ def test_gradient_block_exchange_kernels():
     want = np.zeros_like(g)
     want[np.flatnonzero(mask)] = 2.0 * g[np.flatnonzero(mask)]
     np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("flags", [0, renderer.FLAG_UNPREMULTIPLY, renderer.FLAG_ALPHA_ATLAS, renderer.FLAG_NO_MLP])
+def test_train_rays_matches_oracle_and_the_separate_launches(flags):
+    """snerg_train_rays (render, L2 loss and adjoint per ray in one launch) against the
+    oracle's render and adjoint for dL/dC = 2 (C - C*), and against render_rays +
+    l2_loss + backward on the GPU."""
+    sc0 = synth.make_scene("gauss64")
+    sc = synth.custom_scene(sc0.N, sc0.B, sc0.ind, sc0.atlas, sc0.sigma_max, sc0.mlp, sc0.cameras, flags=flags)
+    rng = np.random.default_rng(17)
+    pix_np = synth.random_pixels(rng, sc.cameras, 3000)
+    target = rng.uniform(size=(pix_np.shape[0], 3)).astype(np.float32)
+    r = renderer.Renderer.from_scene(sc, DEV)
+    pix = torch.from_numpy(pix_np).to(DEV)
+    tg = torch.from_numpy(target).to(DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    ga = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=DEV)
+    gm = torch.zeros(883, dtype=torch.float32, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+    rgb = torch.empty((pix.shape[0], 3), dtype=torch.float32, device=DEV)
+    r.train_rays(sc.cameras, pix, w, tg, ga, gm, loss=loss, out=rgb)
+    r.check_status()
+    o = oracle.render_rays(sc, pix_np)
+    d = o["rgb"] - target
+    ra, rm = oracle.backward_rays(sc, pix_np, 2.0 * d)
+    assert np.abs(rgb.cpu().numpy() - o["rgb"]).max() <= 1e-4
+    np.testing.assert_allclose(float(loss.item()), float((d * d).sum()), rtol=1e-4)
+    assert np.abs(ga.cpu().numpy() - ra).max() <= 1e-4 * np.abs(ra).max()
+    if np.abs(rm).max() > 0:
+        assert np.abs(gm.cpu().numpy() - rm).max() <= 1e-4 * np.abs(rm).max()
+    else:
+        assert (gm.cpu().numpy() == 0).all()
+    # the three separate launches
+    fwd = r.render_rays(sc.cameras, pix, w, aux=True, counts=True)
+    g = torch.empty_like(fwd["rgb"])
+    loss2 = torch.zeros(1, dtype=torch.float32, device=DEV)
+    renderer.l2_loss(fwd["rgb"], tg, g, loss2)
+    ga2 = torch.zeros_like(ga)
+    gm2 = torch.zeros_like(gm)
+    r.backward(sc.cameras, pix, w, g, ga2, gm2, fwd_aux=fwd["aux"], fwd_counts=fwd["counts"])
+    r.check_status()
+    assert torch.allclose(rgb, fwd["rgb"], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(float(loss.item()), float(loss2.item()), rtol=1e-5)
+    assert (ga - ga2).abs().max().item() <= 1e-5 * ga2.abs().max().item()
+    assert (gm - gm2).abs().max().item() <= 1e-5 * max(gm2.abs().max().item(), 1e-30)
+
+
+def test_finetuner_large_batch_takes_the_separate_launches():
+    """A batch larger than one wave of the adjoint kernel goes through render_rays ->
+    l2_loss -> backward; one step gives the same loss and weights as the fused launch."""
+    sc = synth.make_scene("gauss64")
+    rng = np.random.default_rng(19)
+    pix_np = synth.random_pixels(rng, sc.cameras, 4096)
+    target = torch.from_numpy(rng.uniform(size=(4096, 3)).astype(np.float32)).to(DEV)
+    pix = torch.from_numpy(pix_np).to(DEV)
+    r = renderer.Renderer.from_scene(sc, DEV)
+    a = renderer.FineTuner(r, sc.mlp)
+    b = renderer.FineTuner(r, sc.mlp)
+    b.fused_rays = 0
+    la = float(a.step(sc.cameras, pix, target).item())
+    lb = float(b.step(sc.cameras, pix, target).item())
+    np.testing.assert_allclose(la, lb, rtol=1e-5)
+    significant = a.grad.abs() > 1e-3 * a.grad.abs().max()
+    assert torch.allclose(a.mlp[significant], b.mlp[significant], rtol=0, atol=1e-6)
