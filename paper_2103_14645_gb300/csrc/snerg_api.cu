@@ -214,6 +214,10 @@ extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t
 }
 
 namespace snerg {
+// snerg_bwd.cu: one fine-tuning step per ray (render, L2 loss and adjoint in one launch)
+cudaError_t launch_train_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
+                              const float* mlp, const float* target, float* rgb_out, float* loss, float* grad_atlas,
+                              float* grad_mlp, cudaStream_t st);
 // snerg_prep.cu
 cudaError_t launch_requantize_padded(const int32_t* ind, const int32_t* blk_of_slot, const float* values, int64_t nb,
                                      int N, int B, int lgB, uint2* patlas, uint8_t* atlas_out, cudaStream_t st);

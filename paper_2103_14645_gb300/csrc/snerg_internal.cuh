@@ -802,10 +802,6 @@ cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, cons
 cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
                                int64_t n, const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg,
                                cudaStream_t st);
-// one fine-tuning step per ray: render, L2 loss and adjoint in one launch (snerg_bwd.cu)
-cudaError_t launch_train_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
-                              const float* mlp, const float* target, float* rgb_out, float* loss, float* grad_atlas,
-                              float* grad_mlp, cudaStream_t st);
 cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
                                  const float* mlp, const float* grad_rgb, const float* fwd_aux,
                                  const int32_t* fwd_counts, float* grad_atlas, float* grad_mlp, cudaStream_t st);
