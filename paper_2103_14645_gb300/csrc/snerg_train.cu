@@ -4,6 +4,7 @@
 // 3e-4). Together with snerg_render_rays / snerg_render_backward a whole training step
 // runs in this library's kernels.
 #include <cmath>
+#include <cstdint>
 
 #include "snerg_internal.cuh"
 
@@ -77,6 +78,28 @@ __global__ void __launch_bounds__(256) block_copy_kernel(const float4* __restric
     }
 }
 
+// The same update four parameters at a time (16-byte loads and stores) for the bulk of a
+// large parameter array.
+__global__ void __launch_bounds__(256) adam4_kernel(float4* __restrict__ p, float4* __restrict__ m,
+                                                    float4* __restrict__ v, const float4* __restrict__ g, int64_t n4,
+                                                    float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 gi = g[i];
+        float4 mi = m[i], vi = v[i], pi = p[i];
+        const float ga[4] = {gi.x, gi.y, gi.z, gi.w};
+        float ma[4] = {mi.x, mi.y, mi.z, mi.w}, va[4] = {vi.x, vi.y, vi.z, vi.w}, pa[4] = {pi.x, pi.y, pi.z, pi.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ma[k] = b1 * ma[k] + (1.0f - b1) * ga[k];
+            va[k] = b2 * va[k] + (1.0f - b2) * ga[k] * ga[k];
+            pa[k] -= lr * (ma[k] / c1) / (sqrtf(va[k] / c2) + eps);
+        }
+        m[i] = make_float4(ma[0], ma[1], ma[2], ma[3]);
+        v[i] = make_float4(va[0], va[1], va[2], va[3]);
+        p[i] = make_float4(pa[0], pa[1], pa[2], pa[3]);
+    }
+}
+
 static unsigned grid_1d(int64_t n) {
     const int64_t b = (n + 255) / 256;
     return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -103,8 +126,23 @@ extern "C" snerg_status snerg_adam_step(float* d_param, float* d_m, float* d_v, 
     if (!d_param || !d_m || !d_v || !d_grad) return SNERG_E_INVAL;
     const float c1 = (float)(1.0 - std::pow((double)beta1, (double)step));
     const float c2 = (float)(1.0 - std::pow((double)beta2, (double)step));
-    adam_kernel<<<grid_1d(n), 256, 0, (cudaStream_t)stream>>>(d_param, d_m, d_v, d_grad, n, lr, beta1, beta2, eps,
-                                                              c1, c2);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool aligned = (((uintptr_t)d_param | (uintptr_t)d_m | (uintptr_t)d_v | (uintptr_t)d_grad) & 15u) == 0;
+    int64_t done = 0;
+    if (aligned && n >= 4096) {
+        const int64_t n4 = n / 4;
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t want = (n4 + 255) / 256, cap = (int64_t)sms * 8;
+        adam4_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(
+            reinterpret_cast<float4*>(d_param), reinterpret_cast<float4*>(d_m), reinterpret_cast<float4*>(d_v),
+            reinterpret_cast<const float4*>(d_grad), n4, lr, beta1, beta2, eps, c1, c2);
+        done = n4 * 4;
+    }
+    if (done < n)
+        adam_kernel<<<grid_1d(n - done), 256, 0, st>>>(d_param + done, d_m + done, d_v + done, d_grad + done,
+                                                       n - done, lr, beta1, beta2, eps, c1, c2);
     return cudaGetLastError() == cudaSuccess ? SNERG_OK : SNERG_E_CUDA;
 }
 
