@@ -93,3 +93,32 @@ def test_random_scene_parity(seed):
         assert np.abs(gm.cpu().numpy() - rm).max() <= 1e-4 * np.abs(rm).max()
     else:
         assert (gm.cpu().numpy() == 0).all()
+
+
+@pytest.mark.parametrize("seed", range(0, CASES, 3))
+def test_random_scene_fused_training_step(seed):
+    """snerg_train_rays on the random scenes: C, the L2 loss and both gradients against the
+    oracle's render and adjoint for dL/dC = 2 (C - C*)."""
+    sc, rng = _random_scene(seed)
+    r = renderer.Renderer.from_scene(sc, DEV)
+    pix = synth.all_pixels(sc.cameras)
+    n = min(pix.shape[0], 1024)
+    sel = np.ascontiguousarray(pix[rng.choice(pix.shape[0], n, replace=False)])
+    target = rng.uniform(size=(n, 3)).astype(np.float32)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    ga = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=DEV)
+    gm = torch.zeros(synth.MLP_NPARAM, dtype=torch.float32, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+    rgb = torch.empty((n, 3), dtype=torch.float32, device=DEV)
+    r.train_rays(sc.cameras, torch.from_numpy(sel).to(DEV), w, torch.from_numpy(target).to(DEV), ga, gm, loss=loss,
+                 out=rgb)
+    r.check_status()
+    o = oracle.render_rays(sc, sel)
+    d = o["rgb"] - target
+    ra, rm = oracle.backward_rays(sc, sel, 2.0 * d)
+    assert np.abs(rgb.cpu().numpy() - o["rgb"]).max() <= TOL
+    np.testing.assert_allclose(float(loss.item()), float((d * d).sum()), rtol=1e-4)
+    if np.abs(ra).max() > 0:
+        assert np.abs(ga.cpu().numpy() - ra).max() <= 1e-4 * np.abs(ra).max()
+    if np.abs(rm).max() > 0:
+        assert np.abs(gm.cpu().numpy() - rm).max() <= 1e-4 * np.abs(rm).max()
