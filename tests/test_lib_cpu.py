@@ -164,3 +164,30 @@ def test_bake_workspace_and_invalid_arguments(lib):
         g = renderer.bake_field(f["blobs"], f["colors"], f["jitter"])
         mutate(g)
         assert call(g) == 1
+
+
+def test_new_entry_points_reject_bad_arguments_on_host(lib):
+    """snerg_train_rays, snerg_render_to_host and the gradient-block helpers validate their
+    arguments before touching the device."""
+    cams = np.zeros(1, synth.CAMERA_DTYPE)
+    cams["fx"] = cams["fy"] = 1.0
+    cams["W"] = cams["H"] = 4
+    assert lib.snerg_train_rays(None, cams.ctypes.data, 1, 256, 1, 256, 256, None, None, None, None, None) == 1
+    assert lib.snerg_render_to_host(None, cams.ctypes.data, 1, None, None, 256, 4, None) == 1
+    assert lib.snerg_grad_blocks_scatter(256, None, 2, 8, 256, None) == 1
+    assert lib.snerg_grad_blocks_touched(None, 3, 8, 256, None) == 1
+
+
+def test_binding_validates_host_outputs_without_a_gpu():
+    """render_to_host wants a contiguous float32 CPU tensor; these checks run before the
+    library is called."""
+    import torch
+    r = renderer.Renderer.__new__(renderer.Renderer)   # no device state needed for the checks
+    r.nb, r.B = 0, 8
+    cams = synth.orbit_cameras(np.random.default_rng(0), [(4, 4)], synth.CAM_RADIUS)
+    with pytest.raises(ValueError):
+        r.render_to_host(cams, torch.empty((16, 3), dtype=torch.float64))
+    with pytest.raises(ValueError):
+        r.render_to_host(cams, torch.empty((8, 3), dtype=torch.float32))
+    with pytest.raises(ValueError):
+        r.render_to_host(cams, torch.empty((3, 16), dtype=torch.float32).t())
