@@ -130,8 +130,9 @@ typedef struct {
 
 /* Bytes of device workspace snerg_create needs for `num_blocks` occupied macroblocks;
  * 0 if the description is invalid. The workspace holds the apron-padded device copy of
- * the atlas, the indirection grid, two empty-space distance maps (one per block, one per
- * stored voxel) and the status word: about 9 (B+2)^3 bytes per block + 7 (N/B)^3 bytes. */
+ * the atlas, the indirection grid, the empty-space distance maps (per octant of the ray
+ * direction: one per block, one per stored voxel) and the status word: about
+ * 16 (B+2)^3 bytes per block + 35 (N/B)^3 bytes. */
 size_t snerg_workspace_bytes(const snerg_scene_desc* desc, int64_t num_blocks);
 
 /* Build a scene handle (Sec. 5.1 data structure).

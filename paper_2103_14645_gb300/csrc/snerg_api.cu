@@ -63,11 +63,11 @@ bool make_layout(const snerg_scene_desc* d, int64_t nb, Layout* L) {
     const size_t P3 = (size_t)(P * P * P);
     const size_t G3 = (size_t)(G * G * G);
     L->ind = kAlign;                                          // [0, 256): header words
-    L->bdist = align_up(L->ind + G3 * 4);
+    L->bdist = align_up(L->ind + 8 * G3 * 4);                 // one indirection copy per octant
     L->btmp = align_up(L->bdist + G3);                        // 2 G^3 scratch (set-up only)
     L->blk = align_up(L->btmp + 2 * G3);
     L->vskip = align_up(L->blk + (size_t)nb * 4);
-    L->patlas = align_up(L->vskip + (size_t)nb * P3);
+    L->patlas = align_up(L->vskip + 8 * (size_t)nb * P3);    // one voxel plane per octant
     L->total = align_up(L->patlas + (size_t)nb * P3 * 8);
     return true;
 }
@@ -170,20 +170,22 @@ extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { delete h; return SNERG_E_CUDA; }
     if (err != 0) { delete h; return SNERG_E_INVAL; }
-    e = launch_block_distance(ws_ind, G, kBlockDistCap, btmp, btmp + G3, bdist, st);
-    if (e == cudaSuccess) e = launch_voxel_distance(d_atlas, num_blocks, B, vtmp0, vtmp1, vskip, st);
+    // the padded atlas reads occupancy from ws_ind, whose sign every octant copy keeps
+    e = launch_block_distance_octants(ws_ind, G, kBlockDistCap, btmp, btmp + G3, bdist, ws_ind, st);
+    if (e == cudaSuccess) e = launch_voxel_distance_octants(d_atlas, num_blocks, B, vtmp0, vtmp1, vskip, st);
     if (e == cudaSuccess)
         e = launch_build_padded(ws_ind, blk, d_atlas, num_blocks, N, B, ilog2_exact(B), patlas, st);
-    if (e == cudaSuccess) e = launch_fill_vskip_border(vskip, blk, num_blocks, N, B, ilog2_exact(B), st);
-    if (e == cudaSuccess) e = launch_encode_distance(ws_ind, bdist, G3, st);
+    if (e == cudaSuccess) e = launch_fill_vskip_border(vskip, blk, num_blocks, N, B, ilog2_exact(B), 8, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { delete h; return SNERG_E_CUDA; }
-    h->launches = 2 + 5 + (num_blocks > 0 ? 6 : 0);
+    h->launches = 2 + 8 * 5 + (num_blocks > 0 ? 8 * 4 + 1 + 8 : 0);
 
     DevScene& s = h->ds;
     s.ind = ws_ind;
     s.bdist = bdist;
     s.vskip = vskip;
+    s.ind_oct = G3;
+    s.vskip_oct = num_blocks * (int64_t)P * P * P;
     s.patlas = patlas;
     s.status = h->hdr + kHdrStatus;
     s.N = N;

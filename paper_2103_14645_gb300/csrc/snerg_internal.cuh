@@ -14,15 +14,21 @@
 // reproducible bit for bit. Colour arithmetic is ordinary FP32.
 //
 // Device layout (built by snerg_prep.cu inside the caller's workspace):
-//   ind    int32 [G^3]                 indirection (z, y, x): the atlas slot of an occupied
-//                                      block, or -D for an empty one, D >= 1 being the
-//                                      Chebyshev distance (in blocks, capped) to the
-//                                      nearest occupied block -- one load gives both
-//   vskip  uint8 [nb][P^3], P = B + 2  per interior voxel, Chebyshev distance (in voxels)
-//                                      to the nearest voxel of the same block with a
-//                                      non-zero density code; 0 <=> the voxel's own code
-//                                      is non-zero (this plane is the density probe)
+//   ind    int32 [8][G^3]              per octant o of the ray direction (bit i set: d_i
+//                                      < 0), the indirection grid (z, y, x): the atlas slot
+//                                      of an occupied block, or -D for an empty one, D >= 1
+//                                      being the Chebyshev distance (in blocks, capped) to
+//                                      the nearest occupied block in o's cone (the blocks
+//                                      c with c_i - b_i of d_i's sign) -- one load gives both
+//   vskip  uint8 [8][nb][P^3], P = B+2 per octant and interior voxel, Chebyshev distance
+//                                      (in voxels) to the nearest voxel of the same block in
+//                                      the octant's cone with a non-zero density code; 0 <=>
+//                                      the voxel's own code is non-zero (the density probe)
 //   patlas uint2 [nb][P^3]             all 8 channels (density, r, g, b | f0..f3)
+// A ray's lattice coordinates are monotone in the sample index (each step of the binary32
+// lattice arithmetic is a rounded monotone operation), so every later sample's nearest
+// voxel and block lie in the cone of the current one: the one-sided distances are the
+// ones that bound the empty samples ahead.
 // The apron holds the neighbouring blocks' voxels (0 where the neighbour is empty) and
 // the clamped edge voxel at the grid border, so every trilinear stencil of a sample
 // whose nearest voxel lies in block b reads only block b's padded copy.
@@ -59,11 +65,13 @@ constexpr int kAuxCh = 8;
 constexpr int kStatusStepLimit = SNERG_E_STEP_LIMIT;
 
 struct DevScene {
-    const int32_t* ind;
+    const int32_t* ind;    // octant 0's copy; octant o's at ind + o * ind_oct
     const uint8_t* bdist;
-    const uint8_t* vskip;
+    const uint8_t* vskip;  // octant 0's plane; octant o's at vskip + o * vskip_oct
     const uint2* patlas;
     int32_t* status;
+    int64_t ind_oct;       // G^3
+    int64_t vskip_oct;     // nb * P^3
     int32_t N, B, lgB, G, P, P3;
     float fN;         // (float)N
     float scale;      // binary32(N / extent)
@@ -315,6 +323,9 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
     const float m_max = fmaxf(fmaxf(fabsf(r.d[0]), fabsf(r.d[1])), fabsf(r.d[2]));
     const float skip_inv_m = (1.0f - 1.0f / 1048576.0f) / m_max;   // biased down: never overshoots
     const float skip_eps = fmaxf(r.t1, s.fN) * (1.0f / 524288.0f);
+    const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
+    const int32_t* ind = s.ind + oct * s.ind_oct;
+    const uint8_t* vskip = s.vskip + oct * s.vskip_oct;
     int k = k_begin;
     bool done = false;
     if (k_first) *k_first = s.kmax;
@@ -326,18 +337,23 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
 #pragma unroll
         for (int i = 0; i < 3; ++i) b[i] = nearest_voxel(lattice_u(r, t, i), N) >> s.lgB;
         const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
-        const int slot = __ldg(s.ind + bi);
+        const int slot = __ldg(ind + bi);
         st.blocks++;
         if (slot < 0) {
-            // every block within Chebyshev distance D-1 of b is empty: leave that box
+            // every block of the ray's cone within Chebyshev distance D-1 of b is empty:
+            // leave that one-sided box
             const int D1 = -slot - 1;
-            const int lo[3] = {b[0] - D1, b[1] - D1, b[2] - D1};
-            const int hi[3] = {b[0] + D1, b[1] + D1, b[2] + D1};
+            int lo[3], hi[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                lo[i] = ((oct >> i) & 1) ? b[i] - D1 : b[i];
+                hi[i] = ((oct >> i) & 1) ? b[i] : b[i] + D1;
+            }
             k = box_exit(s, r, inv_d, k, lo, hi);
             continue;
         }
         const int kx = box_exit(s, r, inv_d, k, b, b);
-        const uint8_t* vs = s.vskip + (size_t)slot * s.P3;
+        const uint8_t* vs = vskip + (size_t)slot * s.P3;
         const uint2* pa = s.patlas + (size_t)slot * s.P3;
         // block origin minus one, so that the padded local coordinate is floor(u) - o
         const float ox = (float)((b[0] << s.lgB) - 1), oy = (float)((b[1] << s.lgB) - 1),
@@ -358,8 +374,9 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             const int pidx = min(max((int)fmaf(fmaf(lz, Pf, ly), Pf, lx), 0), s.P3 - 1);
             const int vd = __ldg(vs + pidx);
             if (vd != 0) {
-                // no voxel of this block within Chebyshev distance vd-1 has density: the
-                // next s_max samples (s_max*m + eps < vd - 1) are empty, skip them
+                // no voxel of this block in the ray's cone within Chebyshev distance vd-1
+                // has density: the next s_max samples (s_max*m + eps < vd - 1) are empty,
+                // skip them
                 const float q = ((float)vd - 1.0f - skip_eps) * skip_inv_m;
                 kk += max(1, (int)ceilf(q));      // = 1 + s_max, s_max = ceil(q) - 1 >= 0
                 continue;
@@ -811,13 +828,15 @@ cudaError_t launch_build_padded(const int32_t* ind, const int32_t* blk_of_slot, 
                                 int N, int B, int lgB, uint2* patlas, cudaStream_t st);
 // Chebyshev distance maps (three separable passes, distances capped at `cap`):
 // block level over the G^3 indirection grid, voxel level inside each stored block.
+// The render maps are per octant of the ray direction (distances inside its cone).
 cudaError_t launch_block_distance(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
                                   uint8_t* bdist, cudaStream_t st);
-cudaError_t launch_encode_distance(int32_t* ind, const uint8_t* bdist, int64_t n, cudaStream_t st);
+cudaError_t launch_block_distance_octants(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
+                                          uint8_t* bdist, int32_t* ind_oct, cudaStream_t st);
+cudaError_t launch_voxel_distance_octants(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
+                                          uint8_t* vskip, cudaStream_t st);
 cudaError_t launch_fill_vskip_border(uint8_t* vskip, const int32_t* blk_of_slot, int64_t nb, int N, int B, int lgB,
-                                     cudaStream_t st);
-cudaError_t launch_voxel_distance(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
-                                  uint8_t* vskip, cudaStream_t st);
+                                     int n_planes, cudaStream_t st);
 
 struct PersistentParams {
     snerg_camera cams[kMaxCams];

@@ -100,22 +100,33 @@ __global__ void requantize_padded_kernel(const int32_t* __restrict__ ind, const 
 // x, y and z passes out(p) = min over occupied q of max_i |q_i - p_i| (max distributes
 // over min, so the passes compose). The scan walks outwards from p and stops once the
 // offset reaches the best value found, so its cost is the distance itself.
+//
+// `side` restricts q to one half-line (bit 0: q <= p, bit 1: q >= p; 3 = both). With
+// one side per axis the result is the distance to the nearest occupied cell in the
+// octant cone {q : q_i - p_i of the chosen sign}: the cone is a product of half-lines,
+// so the one-sided passes compose the same way.
 // ---------------------------------------------------------------------------------
+constexpr int kSideLow = 1, kSideHigh = 2, kSideBoth = 3;
+
 __device__ __forceinline__ int dt_line(const uint8_t* __restrict__ in, int64_t base, int64_t stride, int pos, int n,
-                                       int cap) {
+                                       int cap, int side) {
     int best = min((int)in[base + pos * stride], cap);
+    const int a_end = (side & kSideLow) ? -1 : pos, b_end = (side & kSideHigh) ? n : pos;
     for (int d = 1; d < best; ++d) {
         const int a = pos - d, b = pos + d;
-        if (a < 0 && b >= n) break;
-        if (a >= 0) best = min(best, max(d, (int)in[base + a * stride]));
-        if (b < n) best = min(best, max(d, (int)in[base + b * stride]));
+        if (a <= a_end && b >= b_end) break;
+        if (a > a_end) best = min(best, max(d, (int)in[base + a * stride]));
+        if (b < b_end) best = min(best, max(d, (int)in[base + b * stride]));
     }
     return best;
 }
 
+// the side of axis i for octant o (bit i of o set: the ray runs towards -i)
+__host__ __device__ __forceinline__ int octant_side(int o, int i) { return ((o >> i) & 1) ? kSideLow : kSideHigh; }
+
 // axis: 0 = x (stride 1), 1 = y (stride n), 2 = z (stride n^2); cubes are contiguous
 __global__ void dt_pass_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int n, int64_t ncubes,
-                               int axis, int cap) {
+                               int axis, int cap, int side) {
     const int64_t n3 = (int64_t)n * n * n;
     const int64_t total = ncubes * n3;
     const int64_t stride = axis == 0 ? 1 : (axis == 1 ? n : (int64_t)n * n);
@@ -125,7 +136,7 @@ __global__ void dt_pass_kernel(const uint8_t* __restrict__ in, uint8_t* __restri
         const int c[3] = {r % n, (r / n) % n, r / (n * n)};
         const int pos = c[axis];
         const int64_t base = t - (int64_t)pos * stride;
-        out[t] = (uint8_t)dt_line(in, base, stride, pos, n, cap);
+        out[t] = (uint8_t)dt_line(in, base, stride, pos, n, cap, side);
     }
 }
 
@@ -143,7 +154,7 @@ __global__ void voxel_seed_kernel(const uint8_t* __restrict__ atlas, int64_t n, 
 
 // z pass of the voxel transform, written into the padded plane (apron cells = 255)
 __global__ void dt_pass_z_padded_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ vskip, int B,
-                                        int64_t nb, int cap) {
+                                        int64_t nb, int cap, int side) {
     const int P = B + 2, P3 = P * P * P;
     const int64_t B3 = (int64_t)B * B * B;
     const int64_t total = nb * P3;
@@ -154,16 +165,20 @@ __global__ void dt_pass_z_padded_kernel(const uint8_t* __restrict__ in, uint8_t*
         uint8_t v = 255;
         if (px >= 0 && py >= 0 && pz >= 0 && px < B && py < B && pz < B) {
             const int64_t base = slot * B3 + (int64_t)py * B + px;
-            v = (uint8_t)dt_line(in, base, (int64_t)B * B, pz, B, cap);
+            v = (uint8_t)dt_line(in, base, (int64_t)B * B, pz, B, cap, side);
         }
         vskip[t] = v;
     }
 }
 
-// ind[i] < 0 (empty) becomes -bdist[i] (>= 1): the march reads one word per block
-__global__ void encode_distance_kernel(int32_t* __restrict__ ind, const uint8_t* __restrict__ bdist, int64_t n) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        if (ind[t] < 0) ind[t] = -(int32_t)max((int)bdist[t], 1);
+// dst[i] = src[i] for an occupied block, -bdist[i] (>= 1) for an empty one: the march
+// reads one word per block. src and dst may be the same array.
+__global__ void encode_distance_kernel(const int32_t* src, const uint8_t* __restrict__ bdist, int32_t* dst,
+                                       int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = src[t];
+        dst[t] = v >= 0 ? v : -(int32_t)max((int)bdist[t], 1);
+    }
 }
 
 // Apron cells of the voxel-distance plane that lie outside the grid get the value of the
@@ -199,26 +214,52 @@ static unsigned grid_for(int64_t n) {
     return (unsigned)(b < 1048576 ? (b > 0 ? b : 1) : 1048576);
 }
 
-cudaError_t launch_block_distance(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
-                                  uint8_t* bdist, cudaStream_t st) {
+static void block_distance(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1, uint8_t* bdist,
+                           const int side[3], cudaStream_t st) {
     const int64_t n = (int64_t)G * G * G;
     block_seed_kernel<<<grid_for(n), 256, 0, st>>>(ind, n, cap, tmp0);
-    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, tmp1, G, 1, 0, cap);
-    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp1, tmp0, G, 1, 1, cap);
-    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, bdist, G, 1, 2, cap);
+    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, tmp1, G, 1, 0, cap, side[0]);
+    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp1, tmp0, G, 1, 1, cap, side[1]);
+    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, bdist, G, 1, 2, cap, side[2]);
+}
+
+cudaError_t launch_block_distance(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
+                                  uint8_t* bdist, cudaStream_t st) {
+    const int both[3] = {kSideBoth, kSideBoth, kSideBoth};
+    block_distance(ind, G, cap, tmp0, tmp1, bdist, both, st);
     return cudaGetLastError();
 }
 
-cudaError_t launch_voxel_distance(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
-                                  uint8_t* vskip, cudaStream_t st) {
+// For each octant o, ind_oct[o] = the indirection grid with every empty entry replaced by
+// -D_o, D_o >= 1 the Chebyshev distance (in blocks, capped) to the nearest occupied block
+// in o's cone. `ind` may be ind_oct[0].
+cudaError_t launch_block_distance_octants(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
+                                          uint8_t* bdist, int32_t* ind_oct, cudaStream_t st) {
+    const int64_t n = (int64_t)G * G * G;
+    for (int o = 7; o >= 0; --o) {          // octant 0 last: ind may alias its copy
+        const int side[3] = {octant_side(o, 0), octant_side(o, 1), octant_side(o, 2)};
+        block_distance(ind, G, cap, tmp0, tmp1, bdist, side, st);
+        encode_distance_kernel<<<grid_for(n), 256, 0, st>>>(ind, bdist, ind_oct + (size_t)o * n, n);
+    }
+    return cudaGetLastError();
+}
+
+// For each octant o, plane o of vskip ([8][nb][P^3]) holds per interior voxel the
+// Chebyshev distance to the nearest voxel of the same block with a non-zero density code
+// in o's cone (apron cells 255; the grid-border apron is filled afterwards).
+cudaError_t launch_voxel_distance_octants(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
+                                          uint8_t* vskip, cudaStream_t st) {
     if (nb <= 0) return cudaSuccess;
     const int64_t n = nb * (int64_t)B * B * B;
+    const int64_t plane = nb * (int64_t)(B + 2) * (B + 2) * (B + 2);
     const int cap = 255;
-    voxel_seed_kernel<<<grid_for(n), 256, 0, st>>>(atlas, n, cap, tmp0);
-    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, tmp1, B, nb, 0, cap);
-    dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp1, tmp0, B, nb, 1, cap);
-    dt_pass_z_padded_kernel<<<grid_for(nb * (int64_t)(B + 2) * (B + 2) * (B + 2)), 256, 0, st>>>(tmp0, vskip, B, nb,
-                                                                                              cap);
+    for (int o = 0; o < 8; ++o) {
+        voxel_seed_kernel<<<grid_for(n), 256, 0, st>>>(atlas, n, cap, tmp0);
+        dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, tmp1, B, nb, 0, cap, octant_side(o, 0));
+        dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp1, tmp0, B, nb, 1, cap, octant_side(o, 1));
+        dt_pass_z_padded_kernel<<<grid_for(plane), 256, 0, st>>>(tmp0, vskip + (size_t)o * plane, B, nb, cap,
+                                                                 octant_side(o, 2));
+    }
     return cudaGetLastError();
 }
 
@@ -249,22 +290,13 @@ cudaError_t launch_requantize_padded(const int32_t* ind, const int32_t* blk_of_s
     return cudaGetLastError();
 }
 
-}  // namespace snerg
-
-namespace snerg {
-cudaError_t launch_encode_distance(int32_t* ind, const uint8_t* bdist, int64_t n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    encode_distance_kernel<<<grid_for(n), 256, 0, st>>>(ind, bdist, n);
-    return cudaGetLastError();
-}
-}  // namespace snerg
-
-namespace snerg {
 cudaError_t launch_fill_vskip_border(uint8_t* vskip, const int32_t* blk_of_slot, int64_t nb, int N, int B, int lgB,
-                                     cudaStream_t st) {
+                                     int n_planes, cudaStream_t st) {
     if (nb <= 0) return cudaSuccess;
-    fill_vskip_border_kernel<<<grid_for(nb * (int64_t)(B + 2) * (B + 2) * (B + 2)), 256, 0, st>>>(vskip, blk_of_slot,
-                                                                                              nb, N, B, lgB);
+    const int64_t plane = nb * (int64_t)(B + 2) * (B + 2) * (B + 2);
+    for (int o = 0; o < n_planes; ++o)
+        fill_vskip_border_kernel<<<grid_for(plane), 256, 0, st>>>(vskip + (size_t)o * plane, blk_of_slot, nb, N, B,
+                                                                  lgB);
     return cudaGetLastError();
 }
 }  // namespace snerg

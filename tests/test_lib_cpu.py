@@ -58,7 +58,7 @@ def test_workspace_bytes(lib):
         d = _desc(N, B)
         got = lib.snerg_workspace_bytes(ctypes.byref(d), nb)
         G, P = N // B, B + 2
-        need = 7 * G ** 3 + 4 * nb + 9 * nb * P ** 3
+        need = 35 * G ** 3 + 4 * nb + 16 * nb * P ** 3
         assert need <= got <= need + 7 * 256
         assert got % 256 == 0
     neg = _desc()
