@@ -154,8 +154,10 @@ __device__ __forceinline__ Ray make_ray(const DevScene& s, const snerg_camera& c
     return r;
 }
 
-__device__ __forceinline__ float lattice_t(const Ray& r, int k) {
-    return __fadd_rn(r.t0, __fadd_rn((float)k, 0.5f));
+// Lattice indices are carried as binary32 integers (exact below 2^24; the index cap is
+// 4N + 16 <= 65,552), so stepping the lattice needs no integer/float conversions.
+__device__ __forceinline__ float lattice_t(const Ray& r, float k) {
+    return __fadd_rn(r.t0, __fadd_rn(k, 0.5f));
 }
 
 __device__ __forceinline__ float lattice_u(const Ray& r, float t, int i) {
@@ -187,7 +189,7 @@ __device__ __forceinline__ Box make_box(const DevScene& s, const int lo[3], cons
 }
 
 // true iff sample k lies before the ray's exit and its nearest voxel's block is in the box
-__device__ __forceinline__ bool in_box(const Ray& r, int k, const Box& bx) {
+__device__ __forceinline__ bool in_box(const Ray& r, float k, const Box& bx) {
     const float t = lattice_t(r, k);
     if (!(t < r.t1)) return false;
 #pragma unroll
@@ -203,36 +205,33 @@ __device__ __forceinline__ bool in_box(const Ray& r, int k, const Box& bx) {
 // rounded monotone operation), so the samples inside a box form one contiguous run:
 // estimate its end from the ray/box exit distance, then confirm or correct it with an
 // exact search on the lattice itself.
-__device__ __forceinline__ int box_exit(const DevScene& s, const Ray& r, const float inv_d[3], int k,
-                                        const int lo[3], const int hi[3]) {
-    const Box bx = make_box(s, lo, hi);
+__device__ __forceinline__ float box_exit(const Ray& r, const float inv_d[3], float kmax, float k, const Box& bx) {
     float te = r.t1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         if (r.d[i] > 0.0f) te = fminf(te, (bx.hi[i] - r.o[i]) * inv_d[i]);
         else if (r.d[i] < 0.0f) te = fminf(te, (bx.lo[i] - r.o[i]) * inv_d[i]);
     }
-    const float kf = ceilf(te - r.t0 - 0.5f);
-    int ke = (kf > (float)s.kmax) ? s.kmax : (kf < 0.0f ? 0 : (int)kf);
-    ke = max(ke, k + 1);
-    int lo_k = k, hi_k;
-    if (ke - 1 > k && !in_box(r, ke - 1, bx)) {
-        hi_k = ke - 1;
-    } else if (ke < s.kmax && in_box(r, ke, bx)) {
+    // estimate clamped to [k + 1, kmax] (fminf/fmaxf also map a NaN estimate into range)
+    const float ke = fmaxf(fminf(ceilf(te - r.t0 - 0.5f), kmax), k + 1.0f);
+    float lo_k = k, hi_k;
+    if (ke - 1.0f > k && !in_box(r, ke - 1.0f, bx)) {
+        hi_k = ke - 1.0f;
+    } else if (ke < kmax && in_box(r, ke, bx)) {
         lo_k = ke;
-        int step = 1;
+        float step = 1.0f;
         for (;;) {
             hi_k = lo_k + step;
-            if (hi_k >= s.kmax) { hi_k = s.kmax; break; }
+            if (hi_k >= kmax) { hi_k = kmax; break; }
             if (!in_box(r, hi_k, bx)) break;
             lo_k = hi_k;
-            step <<= 1;
+            step += step;
         }
     } else {
         return ke;
     }
-    while (hi_k - lo_k > 1) {
-        const int mid = (lo_k + hi_k) >> 1;
+    while (hi_k - lo_k > 1.0f) {
+        const float mid = floorf((lo_k + hi_k) * 0.5f);
         if (in_box(r, mid, bx)) lo_k = mid; else hi_k = mid;
     }
     return hi_k;
@@ -326,11 +325,13 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
     const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
     const int32_t* ind = s.ind + oct * s.ind_oct;
     const uint8_t* vskip = s.vskip + oct * s.vskip_oct;
-    int k = k_begin;
+    const float kmax = (float)s.kmax;
+    float k = (float)k_begin;
+    float steps = 0.0f;
     bool done = false;
     if (k_first) *k_first = s.kmax;
     for (;;) {
-        if (k >= s.kmax) { st.limit = true; break; }
+        if (k >= kmax) { st.limit = true; break; }
         const float t = lattice_t(r, k);
         if (!(t < r.t1)) break;
         int b[3];
@@ -349,17 +350,17 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 lo[i] = ((oct >> i) & 1) ? b[i] - D1 : b[i];
                 hi[i] = ((oct >> i) & 1) ? b[i] : b[i] + D1;
             }
-            k = box_exit(s, r, inv_d, k, lo, hi);
+            k = box_exit(r, inv_d, kmax, k, make_box(s, lo, hi));
             continue;
         }
-        const int kx = box_exit(s, r, inv_d, k, b, b);
+        const float kx = box_exit(r, inv_d, kmax, k, make_box(s, b, b));
         const uint8_t* vs = vskip + (size_t)slot * s.P3;
         const uint2* pa = s.patlas + (size_t)slot * s.P3;
         // block origin minus one, so that the padded local coordinate is floor(u) - o
         const float ox = (float)((b[0] << s.lgB) - 1), oy = (float)((b[1] << s.lgB) - 1),
                     oz = (float)((b[2] << s.lgB) - 1);
         const float Pf = (float)P;
-        int kk = k;
+        float kk = k;
         while (kk < kx) {
             const float tk = lattice_t(r, kk);
             float u[3];
@@ -378,13 +379,13 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 // has density: the next s_max samples (s_max*m + eps < vd - 1) are empty,
                 // skip them
                 const float q = ((float)vd - 1.0f - skip_eps) * skip_inv_m;
-                kk += max(1, (int)ceilf(q));      // = 1 + s_max, s_max = ceil(q) - 1 >= 0
+                kk += fmaxf(1.0f, ceilf(q));      // = 1 + s_max, s_max = ceil(q) - 1 >= 0
                 continue;
             }
             if (TRACE && st.active < trace_cap)
                 trace[st.active] = ((uint64_t)nearest_voxel(u[2], N) * N + (uint64_t)nearest_voxel(u[1], N)) * N +
                                    (uint64_t)nearest_voxel(u[0], N);
-            if (k_first && st.active == 0) *k_first = kk;
+            if (k_first && st.active == 0) *k_first = (int)kk;
             st.active++;
             // trilinear stencil on the virtual grid, cell-centred
             float f[3], g[3], fl[3];
@@ -483,16 +484,17 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 }
             }
             if (saturated) {
-                st.steps += kk - k + 1;
+                steps += kk - k + 1.0f;
                 done = true;
                 break;
             }
-            ++kk;
+            kk += 1.0f;
         }
         if (done) break;
-        st.steps += kx - k;
+        steps += kx - k;
         k = kx;
     }
+    st.steps = (int)steps;
 }
 
 // ---------------------------------------------------------------------------------

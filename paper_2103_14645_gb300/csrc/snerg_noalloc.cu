@@ -88,9 +88,10 @@ __device__ __forceinline__ void march_raw(const DevScene& s, const uint2* atlas,
     float inv_d[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) inv_d[i] = __fdividef(1.0f, r.d[i]);
-    int k = 0;
+    const float kmax = (float)s.kmax;
+    float k = 0.0f;
     for (;;) {
-        if (k >= s.kmax) { st.limit = true; return; }
+        if (k >= kmax) { st.limit = true; return; }
         const float t = lattice_t(r, k);
         if (!(t < r.t1)) return;
         int b[3];
@@ -103,17 +104,17 @@ __device__ __forceinline__ void march_raw(const DevScene& s, const uint2* atlas,
             const int D1 = (int)s.bdist[bi] - 1;
             const int lo[3] = {b[0] - D1, b[1] - D1, b[2] - D1};
             const int hi[3] = {b[0] + D1, b[1] + D1, b[2] + D1};
-            k = box_exit(s, r, inv_d, k, lo, hi);
+            k = box_exit(r, inv_d, kmax, k, make_box(s, lo, hi));
             continue;
         }
-        const int kx = box_exit(s, r, inv_d, k, b, b);
+        const float kx = box_exit(r, inv_d, kmax, k, make_box(s, b, b));
         if (slot >= nb) {                 // entry outside the atlas: reported, read as empty
             atomicCAS(s.status, 0, (int)SNERG_E_INVAL);
             k = kx;
             continue;
         }
         const uint8_t* blk = reinterpret_cast<const uint8_t*>(atlas + (size_t)slot * B * B * B);
-        for (int kk = k; kk < kx; ++kk) {
+        for (float kk = k; kk < kx; kk += 1.0f) {
             const float tk = lattice_t(r, kk);
             float u[3];
             int j[3];
@@ -162,11 +163,11 @@ __device__ __forceinline__ void march_raw(const DevScene& s, const uint2* atlas,
                 st.acc[6] += w * code(cv[c].y, 3);
             }
             if (st.tau > s.taumax) {
-                st.steps += kk - k + 1;
+                st.steps += (int)(kk - k) + 1;
                 return;
             }
         }
-        st.steps += kx - k;
+        st.steps += (int)(kx - k);
         k = kx;
     }
 }
