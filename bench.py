@@ -191,7 +191,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "shell1024: 1024^3 grid, 32^3 blocks, one 800x800 view (seeded quarter of its "
-                                   "rays per step)", "impl": "FP64 C oracle, OpenMP"},
+                                   "rays per step)", "impl": "FP64 C oracle, OpenMP", "scene_checksum": sc.checksum()},
             "cpu_baseline": {"value": round(v, 4), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
                              "sample": f"{n} seeded rays of the 800x800 view per step"},
             "e2e": {"value": round(v, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -331,6 +331,7 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"shell1024: {sc.N}^3 grid, {sc.B}^3 blocks, {sc.occupancy * 100:.1f}% occupied "
                                f"({sc.nb} blocks), one 800x800 view, 39 deg FOV",
+                   "scene_checksum": sc.checksum(),
                    "l2": "flushed before every timed step (256 MiB write)",
                    "launch": "persistent kernel, CUDA-graph replay" if best == "persistent" else "plain (one launch per view)"},
         "launch_modes_ms": {m: round(v[0], 4) for m, v in modes.items()},
@@ -374,7 +375,7 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
     host = torch.empty((n_pix, 3), dtype=torch.float32, pin_memory=True)
     ms_h = time_steps(lambda: r.render(cams, mlp, out=host, persistent=True), reps, 2, stream, flush)
     del host
-    out["batched"] = {"cameras": int(len(cams)), "rays": n_pix,
+    out["batched"] = {"cameras": int(len(cams)), "rays": n_pix, "scene_checksum": bsc.checksum(),
                       "persistent_to_host_mrays_s": round(n_pix / (np.mean(ms_h) * 1e-3) / 1e6, 3),
                       "persistent_mrays_s": round(n_pix / (np.mean(ms_b) * 1e-3) / 1e6, 3),
                       "plain_mrays_s": round(n_pix / (np.mean(ms_p) * 1e-3) / 1e6, 3),
@@ -411,6 +412,7 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
     ms_tr = time_steps(fused, reps, 2, stream, flush)
     n = pix.shape[0]
     out["fwd_bwd"] = {"workload": f"bwd512: {wsc.N}^3 grid, {wsc.occupancy * 100:.1f}% occupied, {n} rays over 8 views",
+                      "scene_checksum": wsc.checksum(),
                       "fwd_mrays_s": round(n / (np.mean(ms_f) * 1e-3) / 1e6, 3),
                       "fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3),
                       "fused_train_mrays_s": round(n / (np.mean(ms_tr) * 1e-3) / 1e6, 3),
@@ -551,6 +553,7 @@ def large_section(args, dev, stream, flush):
     t_b = float(np.mean(ms_b))
     return {"workload": f"shell2048: {sc.N}^3 grid, {sc.B}^3 blocks, {sc.occupancy * 100:.1f}% occupied "
                         f"({sc.nb} blocks), 8 views at 1920x1080 + {n} backward rays",
+            "scene_checksum": sc.checksum(),
             "batched_fwd_mrays_s": round(n_pix / (t_b * 1e-3) / 1e6, 3),
             "batched_fwd_ms": round(t_b, 3),
             "batched_fwd_hbm_frac": round(alg / (t_b * 1e-3) / 1e9 / peak, 4),

@@ -22,6 +22,7 @@ Recipes (all seeded):
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import math
 import os
 from dataclasses import dataclass, field
@@ -114,6 +115,16 @@ class Scene:
     @property
     def n_pixels(self) -> int:
         return int(sum(int(c["W"]) * int(c["H"]) for c in self.cameras))
+
+    def checksum(self) -> str:
+        """SHA-256 (first 16 hex digits) over the grid description, the indirection grid,
+        the atlas codes, the MLP weights and the cameras: identifies the synthetic input."""
+        h = hashlib.sha256()
+        h.update(np.asarray([self.N, self.B], np.int64).tobytes())
+        h.update(np.asarray([*self.bmin, self.extent, self.sigma_max, *self.bg], np.float64).tobytes())
+        for a in (self.ind, self.atlas, self.mlp, self.cameras):
+            h.update(np.ascontiguousarray(a).tobytes())
+        return h.hexdigest()[:16]
 
 
 def init_mlp(rng: np.random.Generator) -> np.ndarray:
