@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
 #pragma unroll
             for (int c = 0; c < 7; ++c) st.acc[c] = __ldg(fwd_aux + kAuxCh * i + c) * 255.0f;
         } else {
-            march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr, 0, &k_first);
+            march<false, false, false, true>(s, r, st, nullptr, 0, nullptr, nullptr, 0, &k_first);
             record_status(s, st);
         }
     }
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
         // the second pass starts at the first composited sample: nothing before it
         // contributes (T = 1 and tau = 0 there), so its weights are the first pass's
         MarchState st2;
-        march<false, true>(s, r, st2, nullptr, 0, gf, grad_atlas, k_first);
+        march<false, true, false, true>(s, r, st2, nullptr, 0, gf, grad_atlas, k_first);
     }
 }
 

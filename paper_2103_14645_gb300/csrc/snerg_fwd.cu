@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(128, 8) render_rays_kernel(const DevScene s, c
     if (DBG && dbg.trace)
         march<true, false>(s, r, st, dbg.trace + i * dbg.trace_cap, dbg.trace_cap, nullptr, nullptr, 0, &k_first);
     else
-        march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr, 0, DBG ? &k_first : nullptr);
+        march<false, false, false, true>(s, r, st, nullptr, 0, nullptr, nullptr, 0, DBG ? &k_first : nullptr);
     record_status(s, st);
     float c[3], aux[kAuxCh];
     finish_ray(s, sW, nullptr, r, st, c, aux, PW ? &pw : nullptr);

@@ -279,6 +279,34 @@ __device__ __forceinline__ void accumulate_colour(MarchState& st, const uint2 cv
     st.acc[6] = a6;
 }
 
+// The trilinear stencil of a sample at u in block-padded coordinates (block origin minus
+// one at o): the fractional weights f, g = 1 - f, the lower corner fl, and the 8 corners'
+// codes (index z*4 + y*2 + x). The lower corner is in [0, B] for a sample of this block
+// (the apron holds the neighbours and the clamped border); the index clamp only guards
+// the address.
+__device__ __forceinline__ void load_stencil(const float u[3], const float o[3], int P, int P3, const uint2* pa,
+                                             float f[3], float g[3], float fl[3], uint2 cv[8]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float x = __fsub_rn(u[i], 0.5f);
+        fl[i] = floorf(x);
+        f[i] = __fsub_rn(x, fl[i]);
+        g[i] = __fsub_rn(1.0f, f[i]);
+    }
+    const int PP = P * P;
+    const float Pf = (float)P;
+    const int i0 = min(max((int)fmaf(fmaf(fl[2] - o[2], Pf, fl[1] - o[1]), Pf, fl[0] - o[0]), 0), P3 - 1 - (PP + P + 1));
+    const uint2* p0 = pa + i0;
+    cv[0] = __ldg(p0);
+    cv[1] = __ldg(p0 + 1);
+    cv[2] = __ldg(p0 + P);
+    cv[3] = __ldg(p0 + P + 1);
+    cv[4] = __ldg(p0 + PP);
+    cv[5] = __ldg(p0 + PP + 1);
+    cv[6] = __ldg(p0 + PP + P);
+    cv[7] = __ldg(p0 + PP + P + 1);
+}
+
 // ---------------------------------------------------------------------------------
 // the march. TRACE records visited voxels; GRAD scatters w_k * trilinear weight * g
 // into the gradient atlas (density frozen, so the weights are the forward ones).
@@ -293,7 +321,7 @@ __device__ __forceinline__ void per_sample_residual(const MlpWeights* pw, const 
 // PS: the non-deferred comparison model (SNERG_FLAG_PER_SAMPLE_MLP): every composited
 // sample also evaluates the view-dependence MLP on its own (c_d, v) (weights from pw, else
 // from sW) and adds w_k (c_d,k + residual_k) to st.rgb_ps.
-template <bool TRACE, bool GRAD, bool PS = false>
+template <bool TRACE, bool GRAD, bool PS = false, bool SPEC = false>
 __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchState& st,
                                       uint64_t* trace, int trace_cap,
                                       const float* gfeat, float* grad_atlas,
@@ -327,6 +355,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
     const uint8_t* vskip = s.vskip + oct * s.vskip_oct;
     const float kmax = (float)s.kmax;
     float k = (float)k_begin;
+    float k_spec = -1.0f;   // the sample after the last composited one
     float steps = 0.0f;
     bool done = false;
     if (k_first) *k_first = s.kmax;
@@ -373,6 +402,16 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             // only guards the address.
             const float lx = floorf(u[0]) - ox, ly = floorf(u[1]) - oy, lz = floorf(u[2]) - oz;
             const int pidx = min(max((int)fmaf(fmaf(lz, Pf, ly), Pf, lx), 0), s.P3 - 1);
+            // SPEC: the sample's stencil is loaded before the probe's answer when the
+            // previous sample was composited (inside a surface the next one usually is
+            // too, and one memory latency then serves both), after it otherwise. It pays
+            // in latency-bound launches (ray lists, the adjoint); where the launch is
+            // issue-bound, lanes that disagree on the guess run the stencil code twice.
+            const float o3[3] = {ox, oy, oz};
+            float f[3], g[3], fl[3];
+            uint2 cv[8];
+            const bool spec = SPEC && (kk == k_spec);
+            if (spec) load_stencil(u, o3, P, s.P3, pa, f, g, fl, cv);
             const int vd = __ldg(vs + pidx);
             if (vd != 0) {
                 // no voxel of this block in the ray's cone within Chebyshev distance vd-1
@@ -388,30 +427,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             if (k_first && st.active == 0) *k_first = (int)kk;
             st.active++;
             // trilinear stencil on the virtual grid, cell-centred
-            float f[3], g[3], fl[3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const float x = __fsub_rn(u[i], 0.5f);
-                fl[i] = floorf(x);
-                f[i] = __fsub_rn(x, fl[i]);
-                g[i] = __fsub_rn(1.0f, f[i]);
-            }
-            // lower stencil corner in padded coordinates, in [0, B] for a sample of this block
-            // (the apron holds the neighbours and the clamped border); the index clamp only
-            // guards the address
-            const int PP = P * P;
-            const int i0 = min(max((int)fmaf(fmaf(fl[2] - oz, Pf, fl[1] - oy), Pf, fl[0] - ox), 0),
-                               s.P3 - 1 - (PP + P + 1));
-            const uint2* p0 = pa + i0;
-            uint2 cv[8];   // index = z*4 + y*2 + x
-            cv[0] = __ldg(p0);
-            cv[1] = __ldg(p0 + 1);
-            cv[2] = __ldg(p0 + P);
-            cv[3] = __ldg(p0 + P + 1);
-            cv[4] = __ldg(p0 + PP);
-            cv[5] = __ldg(p0 + PP + 1);
-            cv[6] = __ldg(p0 + PP + P);
-            cv[7] = __ldg(p0 + PP + P + 1);
+            if (!spec) load_stencil(u, o3, P, s.P3, pa, f, g, fl, cv);
             // binary32 control: density trilinear, x then y then z
             const float e00 = __fadd_rn(__fmul_rn(code(cv[0].x, 0), g[0]), __fmul_rn(code(cv[1].x, 0), f[0]));
             const float e10 = __fadd_rn(__fmul_rn(code(cv[2].x, 0), g[0]), __fmul_rn(code(cv[3].x, 0), f[0]));
@@ -489,6 +505,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 break;
             }
             kk += 1.0f;
+            if (SPEC) k_spec = kk;
         }
         if (done) break;
         steps += kx - k;
