@@ -433,6 +433,7 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
     out["finetune"]["shadow_atlas_values"] = int(fta.shadow.numel())
     del rs, fta
     del rb, ga, gm
+    out["create"] = create_section(sc, dev)
     out["bake"] = bake_section(args, dev, stream, flush)
     out["orbit"] = orbit_section(args, r, sc, dev, stream, flush)
     if not args.no_large:
@@ -485,6 +486,25 @@ def orbit_section(args, r, sc, dev, stream, flush):
             "frames_per_s": round(1e3 / float(ms.mean()), 1),
             "mrays_s": round(800 * 800 / (float(ms.mean()) * 1e-3) / 1e6, 3),
             "paper_webgl_ms_per_frame": 11.9}
+
+
+def create_section(sc, dev):
+    """snerg_create on device-resident inputs: validation, the per-octant distance maps and
+    the padded atlas (the set-up between a bake and the first frame)."""
+    import torch
+    from paper_2103_14645_gb300 import renderer
+    ind = torch.from_numpy(np.ascontiguousarray(sc.ind, np.int32)).to(dev)
+    atl = torch.from_numpy(np.ascontiguousarray(sc.atlas, np.uint8)).to(dev)
+    ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rr = renderer.Renderer(sc.N, sc.B, sc.bmin, sc.extent, sc.sigma_max, sc.bg, ind, atl)
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+        rr.close()
+        del rr
+    return {"workload": f"{sc.name}: {sc.N}^3 grid, {sc.nb} blocks of {sc.B}^3", "ms": round(min(ms), 3)}
 
 
 def bake_section(args, dev, stream, flush):

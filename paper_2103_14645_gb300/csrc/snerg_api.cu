@@ -157,9 +157,8 @@ extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t
     uint8_t* vskip = h->ws + L.vskip;
     uint2* patlas = (uint2*)(h->ws + L.patlas);
     // the voxel distance transform runs before the padded atlas exists and borrows its
-    // region (8 (B+2)^3 >= 2 B^3 bytes per block) as scratch
-    uint8_t* vtmp0 = (uint8_t*)patlas;
-    uint8_t* vtmp1 = vtmp0 + (size_t)num_blocks * B * B * B;
+    // region (8 (B+2)^3 >= 7 B^3 bytes per block) as scratch
+    uint8_t* vscratch = (uint8_t*)patlas;
 
     cudaError_t e = cudaMemsetAsync(h->hdr, 0, kAlign, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ws_ind, d_indirection, (size_t)G3 * 4, cudaMemcpyDeviceToDevice, st);
@@ -172,13 +171,13 @@ extern "C" snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t
     if (err != 0) { delete h; return SNERG_E_INVAL; }
     // the padded atlas reads occupancy from ws_ind, whose sign every octant copy keeps
     e = launch_block_distance_octants(ws_ind, G, kBlockDistCap, btmp, btmp + G3, bdist, ws_ind, st);
-    if (e == cudaSuccess) e = launch_voxel_distance_octants(d_atlas, num_blocks, B, vtmp0, vtmp1, vskip, st);
+    if (e == cudaSuccess) e = launch_voxel_distance_octants(d_atlas, num_blocks, B, vscratch, vskip, st);
     if (e == cudaSuccess)
         e = launch_build_padded(ws_ind, blk, d_atlas, num_blocks, N, B, ilog2_exact(B), patlas, st);
     if (e == cudaSuccess) e = launch_fill_vskip_border(vskip, blk, num_blocks, N, B, ilog2_exact(B), 8, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { delete h; return SNERG_E_CUDA; }
-    h->launches = 2 + 8 * 5 + (num_blocks > 0 ? 8 * 4 + 1 + 8 : 0);
+    h->launches = 2 + 8 * 5 + (num_blocks > 0 ? 15 + 1 + 1 : 0);
 
     DevScene& s = h->ds;
     s.ind = ws_ind;

@@ -852,8 +852,8 @@ cudaError_t launch_block_distance(const int32_t* ind, int G, int cap, uint8_t* t
                                   uint8_t* bdist, cudaStream_t st);
 cudaError_t launch_block_distance_octants(const int32_t* ind, int G, int cap, uint8_t* tmp0, uint8_t* tmp1,
                                           uint8_t* bdist, int32_t* ind_oct, cudaStream_t st);
-cudaError_t launch_voxel_distance_octants(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
-                                          uint8_t* vskip, cudaStream_t st);
+cudaError_t launch_voxel_distance_octants(const uint8_t* atlas, int64_t nb, int B, uint8_t* scratch, uint8_t* vskip,
+                                          cudaStream_t st);
 cudaError_t launch_fill_vskip_border(uint8_t* vskip, const int32_t* blk_of_slot, int64_t nb, int N, int B, int lgB,
                                      int n_planes, cudaStream_t st);
 

@@ -184,13 +184,15 @@ __global__ void encode_distance_kernel(const int32_t* src, const uint8_t* __rest
 // Apron cells of the voxel-distance plane that lie outside the grid get the value of the
 // voxel they clamp to (clamp-to-edge, as in the padded atlas). A sample that rounding puts
 // a hair outside the grid then finds its clamped nearest voxel's value without a clamp.
+// (n_planes planes of [nb][P^3] one after the other; each is filled from itself)
 __global__ void fill_vskip_border_kernel(uint8_t* __restrict__ vskip, const int32_t* __restrict__ blk_of_slot,
-                                         int64_t nb, int N, int B, int lgB) {
+                                         int64_t nb, int N, int B, int lgB, int n_planes) {
     const int P = B + 2, P3 = P * P * P, G = N >> lgB;
-    const int64_t total = nb * (int64_t)P3;
+    const int64_t total = n_planes * nb * (int64_t)P3;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t slot = t / P3;
-        const int r = (int)(t - slot * P3);
+        const int64_t ps = t / P3;                       // plane * nb + slot
+        const int64_t slot = ps % nb;
+        const int r = (int)(t - ps * P3);
         const int p[3] = {r % P, (r / P) % P, r / (P * P)};
         if (p[0] >= 1 && p[0] <= B && p[1] >= 1 && p[1] <= B && p[2] >= 1 && p[2] <= B) continue;   // interior
         const int blk = blk_of_slot[slot];
@@ -205,7 +207,7 @@ __global__ void fill_vskip_border_kernel(uint8_t* __restrict__ vskip, const int3
             if (g >= 0 && g < N) { ok = false; break; }      // faces an interior neighbour: never probed
             q[i] = min(max(g, 0), N - 1) - b[i] * B + 1;     // the clamped voxel, inside this block
         }
-        if (ok) vskip[t] = vskip[slot * P3 + (q[2] * P + q[1]) * P + q[0]];
+        if (ok) vskip[t] = vskip[ps * P3 + (q[2] * P + q[1]) * P + q[0]];
     }
 }
 
@@ -246,20 +248,26 @@ cudaError_t launch_block_distance_octants(const int32_t* ind, int G, int cap, ui
 
 // For each octant o, plane o of vskip ([8][nb][P^3]) holds per interior voxel the
 // Chebyshev distance to the nearest voxel of the same block with a non-zero density code
-// in o's cone (apron cells 255; the grid-border apron is filled afterwards).
-cudaError_t launch_voxel_distance_octants(const uint8_t* atlas, int64_t nb, int B, uint8_t* tmp0, uint8_t* tmp1,
-                                          uint8_t* vskip, cudaStream_t st) {
+// in o's cone (apron cells 255; the grid-border apron is filled afterwards). The x pass
+// depends only on o's x side, the y pass on its x and y sides, so the eight transforms
+// share them: 2 x passes, 4 y passes, 8 z passes. `scratch` holds 7 nb B^3 bytes.
+cudaError_t launch_voxel_distance_octants(const uint8_t* atlas, int64_t nb, int B, uint8_t* scratch, uint8_t* vskip,
+                                          cudaStream_t st) {
     if (nb <= 0) return cudaSuccess;
     const int64_t n = nb * (int64_t)B * B * B;
     const int64_t plane = nb * (int64_t)(B + 2) * (B + 2) * (B + 2);
     const int cap = 255;
-    for (int o = 0; o < 8; ++o) {
-        voxel_seed_kernel<<<grid_for(n), 256, 0, st>>>(atlas, n, cap, tmp0);
-        dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp0, tmp1, B, nb, 0, cap, octant_side(o, 0));
-        dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(tmp1, tmp0, B, nb, 1, cap, octant_side(o, 1));
-        dt_pass_z_padded_kernel<<<grid_for(plane), 256, 0, st>>>(tmp0, vskip + (size_t)o * plane, B, nb, cap,
-                                                                 octant_side(o, 2));
-    }
+    uint8_t* seed = scratch;
+    uint8_t* xs = scratch + n;          // [2][n]: x side (bit 0 of o)
+    uint8_t* ys = scratch + 3 * n;      // [4][n]: x and y sides (bits 0, 1 of o)
+    voxel_seed_kernel<<<grid_for(n), 256, 0, st>>>(atlas, n, cap, seed);
+    for (int a = 0; a < 2; ++a)
+        dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(seed, xs + a * n, B, nb, 0, cap, octant_side(a, 0));
+    for (int a = 0; a < 4; ++a)
+        dt_pass_kernel<<<grid_for(n), 256, 0, st>>>(xs + (a & 1) * n, ys + a * n, B, nb, 1, cap, octant_side(a, 1));
+    for (int o = 0; o < 8; ++o)
+        dt_pass_z_padded_kernel<<<grid_for(plane), 256, 0, st>>>(ys + (o & 3) * n, vskip + (size_t)o * plane, B, nb,
+                                                                 cap, octant_side(o, 2));
     return cudaGetLastError();
 }
 
@@ -293,10 +301,8 @@ cudaError_t launch_requantize_padded(const int32_t* ind, const int32_t* blk_of_s
 cudaError_t launch_fill_vskip_border(uint8_t* vskip, const int32_t* blk_of_slot, int64_t nb, int N, int B, int lgB,
                                      int n_planes, cudaStream_t st) {
     if (nb <= 0) return cudaSuccess;
-    const int64_t plane = nb * (int64_t)(B + 2) * (B + 2) * (B + 2);
-    for (int o = 0; o < n_planes; ++o)
-        fill_vskip_border_kernel<<<grid_for(plane), 256, 0, st>>>(vskip + (size_t)o * plane, blk_of_slot, nb, N, B,
-                                                                  lgB);
+    fill_vskip_border_kernel<<<grid_for(n_planes * nb * (int64_t)(B + 2) * (B + 2) * (B + 2)), 256, 0, st>>>(
+        vskip, blk_of_slot, nb, N, B, lgB, n_planes);
     return cudaGetLastError();
 }
 }  // namespace snerg
