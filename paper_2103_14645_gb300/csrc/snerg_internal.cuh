@@ -200,20 +200,53 @@ __device__ __forceinline__ bool in_box(const Ray& r, float k, const Box& bx) {
     return true;
 }
 
+// The margin (in samples) of box_exit's unconfirmed estimate for ray r in a grid of N
+// voxels per axis, with t_m = max(t1, 1) bounding every lattice t the march compares:
+//  - the estimate K = fl(fl(te - t0) - 0.5) with te = fl(fl(face - o) * inv_d), inv_d
+//    within 2 ulp of 1/d: |K - K*| <= t_m (2^-22 + 2^-23 + 2^-24 + 2 * 2^-24) < t_m 2^-20;
+//  - a lattice coordinate u = fl(o + fl(t d)), t = fl(t0 + k + 1/2), lies within
+//    (2 t_m |d_i| + |u|) 2^-24 of its exact value, |u| <= N + 1 near a face, and moves by
+//    |d_i| per sample: at most (2 t_m + (N + 1) / |d_i|) 2^-24 samples on axis i, and
+//    t_m 2^-24 samples for the test t < t1;
+// taken four times over. A component of d that is zero makes no face ahead; a tiny one
+// makes the margin large and the exact search runs instead.
+__device__ __forceinline__ float exit_margin(const Ray& r, float fN) {
+    float dmin = INFINITY;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        if (r.d[i] != 0.0f) dmin = fminf(dmin, fabsf(r.d[i]));
+    const float tm = fmaxf(r.t1, 1.0f);
+    const float lat = (2.0f * tm + (fN + 1.0f) / dmin) * (1.0f / 16777216.0f);
+    return 4.0f * (tm * (1.0f / 1048576.0f) + lat + tm * (1.0f / 16777216.0f));
+}
+
 // First lattice index k' > k with in_box(k') false, given in_box(k). Each axis's
 // nearest voxel is a monotone function of k (every step of the lattice arithmetic is a
 // rounded monotone operation), so the samples inside a box form one contiguous run:
 // estimate its end from the ray/box exit distance, then confirm or correct it with an
 // exact search on the lattice itself.
-__device__ __forceinline__ float box_exit(const Ray& r, const float inv_d[3], float kmax, float k, const Box& bx) {
+//
+// The estimate needs no confirmation when the real crossing index is at least `margin`
+// from every integer, margin bounding (a) the error of the estimate K (rounding of the
+// face distances, the approximate reciprocal, the two subtractions) and (b) how far in k
+// the binary32 lattice can place a sample across a face or past t1 from where exact
+// arithmetic would (see exit_margin). Then every sample before ceil(K) is inside on every
+// face still ahead (their crossings are no earlier than K's) and the sample at ceil(K)
+// is outside. A margin of 1 or more disables this.
+__device__ __forceinline__ float box_exit(const Ray& r, const float inv_d[3], float kmax, float k, const Box& bx,
+                                          float margin) {
     float te = r.t1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         if (r.d[i] > 0.0f) te = fminf(te, (bx.hi[i] - r.o[i]) * inv_d[i]);
         else if (r.d[i] < 0.0f) te = fminf(te, (bx.lo[i] - r.o[i]) * inv_d[i]);
     }
+    const float K = te - r.t0 - 0.5f;
+    const float n = ceilf(K);
+    const float fr = n - K;                   // in [0, 1); exact for |K| >= 1 (Sterbenz)
+    if (n >= k + 1.0f && n < kmax && fr >= margin && fr < 1.0f - margin) return n;
     // estimate clamped to [k + 1, kmax] (fminf/fmaxf also map a NaN estimate into range)
-    const float ke = fmaxf(fminf(ceilf(te - r.t0 - 0.5f), kmax), k + 1.0f);
+    const float ke = fmaxf(fminf(n, kmax), k + 1.0f);
     float lo_k = k, hi_k;
     if (ke - 1.0f > k && !in_box(r, ke - 1.0f, bx)) {
         hi_k = ke - 1.0f;
@@ -350,6 +383,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
     const float m_max = fmaxf(fmaxf(fabsf(r.d[0]), fabsf(r.d[1])), fabsf(r.d[2]));
     const float skip_inv_m = (1.0f - 1.0f / 1048576.0f) / m_max;   // biased down: never overshoots
     const float skip_eps = fmaxf(r.t1, s.fN) * (1.0f / 524288.0f);
+    const float exit_m = exit_margin(r, s.fN);
     const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
     const int32_t* ind = s.ind + oct * s.ind_oct;
     const uint8_t* vskip = s.vskip + oct * s.vskip_oct;
@@ -379,10 +413,10 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 lo[i] = ((oct >> i) & 1) ? b[i] - D1 : b[i];
                 hi[i] = ((oct >> i) & 1) ? b[i] : b[i] + D1;
             }
-            k = box_exit(r, inv_d, kmax, k, make_box(s, lo, hi));
+            k = box_exit(r, inv_d, kmax, k, make_box(s, lo, hi), exit_m);
             continue;
         }
-        const float kx = box_exit(r, inv_d, kmax, k, make_box(s, b, b));
+        const float kx = box_exit(r, inv_d, kmax, k, make_box(s, b, b), exit_m);
         const uint8_t* vs = vskip + (size_t)slot * s.P3;
         const uint2* pa = s.patlas + (size_t)slot * s.P3;
         // block origin minus one, so that the padded local coordinate is floor(u) - o

@@ -89,6 +89,7 @@ __device__ __forceinline__ void march_raw(const DevScene& s, const uint2* atlas,
 #pragma unroll
     for (int i = 0; i < 3; ++i) inv_d[i] = __fdividef(1.0f, r.d[i]);
     const float kmax = (float)s.kmax;
+    const float exit_m = exit_margin(r, s.fN);
     float k = 0.0f;
     for (;;) {
         if (k >= kmax) { st.limit = true; return; }
@@ -104,10 +105,10 @@ __device__ __forceinline__ void march_raw(const DevScene& s, const uint2* atlas,
             const int D1 = (int)s.bdist[bi] - 1;
             const int lo[3] = {b[0] - D1, b[1] - D1, b[2] - D1};
             const int hi[3] = {b[0] + D1, b[1] + D1, b[2] + D1};
-            k = box_exit(r, inv_d, kmax, k, make_box(s, lo, hi));
+            k = box_exit(r, inv_d, kmax, k, make_box(s, lo, hi), exit_m);
             continue;
         }
-        const float kx = box_exit(r, inv_d, kmax, k, make_box(s, b, b));
+        const float kx = box_exit(r, inv_d, kmax, k, make_box(s, b, b), exit_m);
         if (slot >= nb) {                 // entry outside the atlas: reported, read as empty
             atomicCAS(s.status, 0, (int)SNERG_E_INVAL);
             k = kx;
