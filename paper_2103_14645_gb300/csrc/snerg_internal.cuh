@@ -463,18 +463,14 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             st.active++;
             // trilinear stencil on the virtual grid, cell-centred
             if (!spec) load_stencil(u, o3, P, s.P3, pa, f, g, fl, cv);
-            // binary32 control: density trilinear, x then y then z:
-            //   e00 = c0 g0 + c1 f0, e10 = c2 g0 + c3 f0, e01 = c4 g0 + c5 f0, e11 = c6 g0 + c7 f0,
-            //   e0 = e00 g1 + e10 f1, e1 = e01 g1 + e11 f1, sq = e0 g2 + e1 f2,
-            // two at a time in packed pairs (each element rounded exactly as the scalar form)
-            const float2 gx = make_float2(g[0], g[0]), fx = make_float2(f[0], f[0]);
-            const float2 e00_10 = __fadd2_rn(__fmul2_rn(code2(cv[0].x, 0, cv[2].x, 0), gx),
-                                             __fmul2_rn(code2(cv[1].x, 0, cv[3].x, 0), fx));
-            const float2 e01_11 = __fadd2_rn(__fmul2_rn(code2(cv[4].x, 0, cv[6].x, 0), gx),
-                                             __fmul2_rn(code2(cv[5].x, 0, cv[7].x, 0), fx));
-            const float2 e0_1 = __fadd2_rn(__fmul2_rn(make_float2(e00_10.x, e01_11.x), make_float2(g[1], g[1])),
-                                           __fmul2_rn(make_float2(e00_10.y, e01_11.y), make_float2(f[1], f[1])));
-            const float sq = __fadd_rn(__fmul_rn(e0_1.x, g[2]), __fmul_rn(e0_1.y, f[2]));
+            // binary32 control: density trilinear, x then y then z
+            const float e00 = __fadd_rn(__fmul_rn(code(cv[0].x, 0), g[0]), __fmul_rn(code(cv[1].x, 0), f[0]));
+            const float e10 = __fadd_rn(__fmul_rn(code(cv[2].x, 0), g[0]), __fmul_rn(code(cv[3].x, 0), f[0]));
+            const float e01 = __fadd_rn(__fmul_rn(code(cv[4].x, 0), g[0]), __fmul_rn(code(cv[5].x, 0), f[0]));
+            const float e11 = __fadd_rn(__fmul_rn(code(cv[6].x, 0), g[0]), __fmul_rn(code(cv[7].x, 0), f[0]));
+            const float e0 = __fadd_rn(__fmul_rn(e00, g[1]), __fmul_rn(e10, f[1]));
+            const float e1 = __fadd_rn(__fmul_rn(e01, g[1]), __fmul_rn(e11, f[1]));
+            const float sq = __fadd_rn(__fmul_rn(e0, g[2]), __fmul_rn(e1, f[2]));
             // compositing (Eqs. 2, 5, 6)
             float wk;
             bool saturated;
