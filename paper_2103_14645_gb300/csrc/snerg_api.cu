@@ -390,8 +390,7 @@ static snerg_status render_persistent(snerg_scene* h, const snerg_camera* cams, 
     static const MlpWeights zero_w = {};
     const MlpWeights* w_arg = pw ? pw : &zero_w;
     void* args[] = {(void*)&ds, (void*)p, (void*)&mlp_arg, (void*)w_arg, (void*)&rgb_arg, (void*)&queue};
-    cudaKernelNodeParams kp;
-    std::memset(&kp, 0, sizeof(kp));
+    cudaKernelNodeParams kp = {};
     kp.func = const_cast<void*>(persistent_kernel_fn(pw != nullptr));
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(cfg.block);
