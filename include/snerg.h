@@ -296,7 +296,9 @@ snerg_status snerg_adam_step(float* d_param, float* d_m, float* d_v, const float
  * device array of 786,688 bytes that every GPU loading this library holds until the
  * process exits. The first call on each device looks up that array's device address
  * (cudaGetSymbolAddress, with the device current): make that first call before any
- * stream capture. All calls share the array and each call rewrites it, so calls whose
+ * stream capture. The address is kept for the life of the process, so do not use this
+ * entry point after a device reset (cudaDeviceReset or a primary-context reset may move
+ * the array). All calls share the array and each call rewrites it, so calls whose
  * work overlaps on the GPU (different streams or host threads) race; serialise them.
  * Asynchronous on `stream`. */
 snerg_status snerg_render_rays_noalloc(const snerg_scene_desc* desc, const int32_t* d_indirection,

@@ -12,7 +12,10 @@
 //
 // The array's host-side name is only a stand-in; its device address is fetched with
 // cudaGetSymbolAddress once per device (with that device current) on the first call
-// made on that device, so that first call should happen before any stream capture.
+// made on that device, so that first call should happen before any stream capture. The
+// address is kept for the life of the process: a device reset (cudaDeviceReset, or a
+// reset of the primary context) reloads the module and may move the array, after which
+// the kept address is stale, so this entry point must not be used across a reset.
 // Every call shares the array: calls whose work overlaps on the GPU (two streams, or two
 // host threads) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
@@ -71,8 +74,9 @@ __device__ __forceinline__ uint2 raw_voxel(const DevScene& s, const uint2* atlas
 // The march of snerg_internal.cuh on the caller's unpadded atlas: empty blocks are
 // skipped through the block distance map, every lattice sample of an occupied block
 // probes its nearest voxel's density code, and the 8 trilinear corners are fetched
-// through the indirection grid. Same lattice, same binary32 control arithmetic, same
-// compositing order.
+// through the indirection grid. Same lattice, same binary32 control arithmetic (so the
+// same composited samples and the same early exit), and the same colour accumulation
+// (accumulate_colour).
 __device__ __forceinline__ void march_raw(const DevScene& s, const uint2* atlas, int64_t nb, const Ray& r,
                                           MarchState& st) {
 #pragma unroll
@@ -152,17 +156,7 @@ __device__ __forceinline__ void march_raw(const DevScene& s, const uint2* atlas,
             const float e = expf(-od);
             const float wk = st.T * (1.0f - e);
             st.T *= e;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float w = wk * (((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]));
-                st.acc[0] += w * code(cv[c].x, 1);
-                st.acc[1] += w * code(cv[c].x, 2);
-                st.acc[2] += w * code(cv[c].x, 3);
-                st.acc[3] += w * code(cv[c].y, 0);
-                st.acc[4] += w * code(cv[c].y, 1);
-                st.acc[5] += w * code(cv[c].y, 2);
-                st.acc[6] += w * code(cv[c].y, 3);
-            }
+            accumulate_colour(st, cv, wk, f, g);
             if (st.tau > s.taumax) {
                 st.steps += (int)(kk - k) + 1;
                 return;

@@ -7,8 +7,10 @@ checking samples on the lattice. This test replays that arithmetic with numpy fl
 (one rounding per operation, as the kernel's binary32 control arithmetic does), with the
 reciprocal of each direction component perturbed by up to 2 ulp (the error bound of the
 approximate reciprocal the kernel uses), on random rays and on rays built so that a face
-crossing falls within 1e-3 samples of a lattice point. Whenever the estimate is taken it
-must equal the first index found by stepping the lattice one sample at a time."""
+crossing falls within 1e-3 samples of a lattice point, and on rays whose first face
+crossing comes before the second sample (an estimate K in (0, 1), where the fraction
+1 - K of K < 1/2 is rounded). Whenever the estimate is taken it must equal the first
+index found by stepping the lattice one sample at a time."""
 
 import numpy as np
 import pytest
@@ -58,7 +60,7 @@ def _estimate(o, d, inv_d, t0, t1, lo, hi):
     return n, F(n - K)
 
 
-def _case(rng, N, B, adversarial):
+def _case(rng, N, B, mode):
     d = rng.normal(size=3)
     if rng.uniform() < 0.3:                     # near an axis or a face plane
         d[rng.integers(0, 3)] *= 10.0 ** rng.uniform(-6, -1)
@@ -66,7 +68,19 @@ def _case(rng, N, B, adversarial):
     t0 = F(0.0)
     k = int(rng.integers(0, 4 * N))
     o = rng.uniform(0, N, 3).astype(F)
-    if adversarial:
+    if mode == "near_start":
+        # the ray starts inside the grid and crosses a face of its first block at
+        # t = K + 1/2 with K in (0, 1), mostly below 1/2
+        i = int(np.argmax(np.abs(d)))
+        k = 0
+        K = rng.uniform(0.0, 0.5) if rng.uniform() < 0.75 else rng.uniform(0.5, 1.0)
+        b = int(rng.integers(1, N // B - 1))
+        face = b * B + (B if d[i] > 0 else 0)
+        o[i] = F(face - (K + 0.5) * float(d[i]))
+        for j in range(3):
+            if j != i:
+                o[j] = F(rng.uniform(B, N - B))
+    elif mode == "adversarial":
         # put the crossing of one face of the block of sample k within 1e-3 of a lattice index
         i = int(np.argmax(np.abs(d)))
         kt = k + int(rng.integers(1, 3 * B))
@@ -107,14 +121,15 @@ def _case(rng, N, B, adversarial):
     return o, d, t0, t1, k, lo, hi
 
 
-@pytest.mark.parametrize("N,B,n_cases,adversarial", [(64, 8, 1500, False), (256, 32, 1500, False),
-                                                     (1024, 32, 1500, True), (2048, 32, 1000, True)])
-def test_unconfirmed_exit_matches_the_lattice(N, B, n_cases, adversarial):
-    rng = np.random.default_rng(N + (7 if adversarial else 0))
+@pytest.mark.parametrize("N,B,n_cases,mode", [(64, 8, 1500, "random"), (256, 32, 1500, "random"),
+                                              (1024, 32, 1500, "adversarial"), (2048, 32, 1000, "adversarial"),
+                                              (1024, 32, 1500, "near_start")])
+def test_unconfirmed_exit_matches_the_lattice(N, B, n_cases, mode):
+    rng = np.random.default_rng(N + {"random": 0, "adversarial": 7, "near_start": 13}[mode])
     kmax = 4 * N + 16
-    taken = checked = 0
+    taken = checked = below_half = 0
     while checked < n_cases:
-        c = _case(rng, N, B, adversarial)
+        c = _case(rng, N, B, mode)
         if c is None:
             continue
         o, d, t0, t1, k, lo, hi = c
@@ -125,8 +140,12 @@ def test_unconfirmed_exit_matches_the_lattice(N, B, n_cases, adversarial):
         if not (n >= k + 1 and n < kmax and fr >= m and fr < 1 - m):
             continue
         taken += 1
+        if mode == "near_start":
+            below_half += bool(n == 1 and F(1) - fr < F(0.5))
         exact = k + 1
         while exact < kmax and _in_box(o, d, t0, t1, exact, lo, hi):
             exact += 1
         assert n == exact, (o, d, t0, t1, k, lo, hi, n, exact)
     assert taken > n_cases // 2          # the estimate is taken in most cases
+    if mode == "near_start":
+        assert below_half > n_cases // 4    # and often with a rounded fraction (K < 1/2)
