@@ -34,27 +34,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mrays/s & 800² frames/s, batched vs plain; fwd+bwd Mrays/s; % HBM roofline"
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "render_image_shell1024.md")
 CSRC = os.path.join(ROOT, "paper_2103_14645_gb300", "csrc")
 
+# the sources each profiled kernel is compiled from (march core + its launcher)
+FWD_SOURCES = ("snerg_internal.cuh", "snerg_fwd.cu")
+BWD_SOURCES = ("snerg_internal.cuh", "snerg_bwd.cu")
 
-# the sources the forward render kernels are compiled from (march core + launchers)
-RENDER_SOURCES = ("snerg_internal.cuh", "snerg_fwd.cu")
 
-
-def kernel_source_digest() -> str:
+def kernel_source_digest(sources=FWD_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in RENDER_SOURCES:
+    for f in sources:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
+def profiled_traffic(profile: str, sources=FWD_SOURCES):
+    """DRAM bytes per launch from the committed ncu summary profiles/<profile>.md, if it
+    was taken on the current kernel sources (else None)."""
     try:
-        with open(PROFILE_TRAFFIC) as f:
+        with open(os.path.join(ROOT, "profiles", profile + ".md")) as f:
             txt = f.read()
     except OSError:
         return None
@@ -63,12 +62,39 @@ def profiled_traffic():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_digest") != kernel_source_digest():
+    if vals.get("kernel_source_digest") != kernel_source_digest(sources):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def march_bytes(cnt, rays):
+    """Algorithmic bytes of a forward march (per launch): 4 B per indirection entry read,
+    1 B per lattice sample in an occupied block (the density probe), 64 B per composited
+    sample (8 corners x 8 channels), 12 B of output colour per ray. cnt = column sums of
+    the debug counts (steps, composited, indirection reads)."""
+    return 4.0 * cnt[2] + 1.0 * cnt[0] + 64.0 * cnt[1] + 12.0 * rays
+
+
+# adjoint per composited sample: the stencil again (64 B) and two 16-byte vector atomics
+# per corner into the gradient atlas, each a read and a write at the L2 (8 x 2 x 32 B)
+ADJ_BYTES_PER_SAMPLE = 64 + 8 * 2 * 32
+MLP_GRAD_BYTES_PER_CTA = 883 * 4 * 2      # one atomic per parameter per CTA (read + write)
+
+
+def roofline(alg_bytes, ms, kernel, profile=None, sources=FWD_SOURCES, launches=1):
+    """The roofline object of one timed launch (or `launches` launches per step): counted
+    algorithmic bytes over the mean CUDA-event time, against the measured HBM copy peak."""
+    peaks, src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic(profile, sources) if profile else None,
+            "peak_source": f"{src} hbm_gbs", "kernel": kernel, "launches_per_step": launches,
+            ("algorithmic_bytes_per_launch" if launches == 1 else "algorithmic_bytes_per_step"): int(alg_bytes)}
 
 
 def measured_peaks():
@@ -257,8 +283,8 @@ def run_ours(args, ws, rank, local):
     dbg = r.render(cams, mlp, counts=True)
     r.check_status()
     cnt = dbg["counts"].double().sum(0).cpu().numpy()
-    steps_tot, active_tot, blocks_tot = cnt[0], cnt[1], cnt[2]
-    alg_bytes = 4 * blocks_tot + 1 * steps_tot + 64 * active_tot + 12 * n_rays
+    alg_bytes = march_bytes(cnt, n_rays)
+    del dbg
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -321,10 +347,9 @@ def run_ours(args, ws, rank, local):
         if dist:
             tdist.destroy_process_group()
         return
-    peaks, src = measured_peaks()
-    peak = float(peaks["hbm_gbs"])
-    achieved = alg_bytes / (t_step * 1e-3) / 1e9
-    traffic = profiled_traffic()
+    kname = "render_persistent_kernel" if best == "persistent" else "render_image_kernel"
+    rl = roofline(alg_bytes, t_step, kname,
+                  profile="render_persistent_shell1024" if best == "persistent" else "render_image_shell1024")
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max, 4), "higher_is_better": True, "scaling": "weak",
@@ -336,10 +361,7 @@ def run_ours(args, ws, rank, local):
                    "launch": "persistent kernel, CUDA-graph replay" if best == "persistent" else "plain (one launch per view)"},
         "launch_modes_ms": {m: round(v[0], 4) for m, v in modes.items()},
         "frames_per_s": round(1e3 / t_max, 2),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "peak_source": f"{src} hbm_gbs", "kernel": "render_image_kernel",
-                     "algorithmic_bytes_per_launch": int(alg_bytes)},
+        "roofline": rl,
         "e2e": {"value": round(e2e, 3), "unit": "Mrays/s", "h2d_bytes_per_step": 80 * len(cams),
                 "d2h_bytes_per_step": n_rays * 12},
         "gpu_launches": int(launches),
@@ -363,8 +385,12 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
     n_pix = bsc.n_pixels
     r.set_mlp(bsc.mlp)
     mlp = None
-    buf = torch.empty((n_pix, 3), dtype=torch.float32, device=dev)
     reps = max(3, min(args.steps, 10))
+    # counted algorithmic bytes of the batch (untimed debug render of the 64 cameras)
+    dbg = r.render(cams, mlp, counts=True)
+    cnt_b = dbg["counts"].double().sum(0).cpu().numpy()
+    del dbg
+    buf = torch.empty((n_pix, 3), dtype=torch.float32, device=dev)
     barrier()
     ms_b = time_steps(lambda: r.render(cams, mlp, out=buf, persistent=True), reps, 2, stream, flush)
     ms_p = time_steps(lambda: r.render(cams, mlp, out=buf), reps, 2, stream, flush)
@@ -381,7 +407,11 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
                       "plain_mrays_s": round(n_pix / (np.mean(ms_p) * 1e-3) / 1e6, 3),
                       "ratio": round(float(np.mean(ms_p) / np.mean(ms_b)), 4),
                       "tile": [tw, th], "ctas_per_sm": c,
-                      "ms_persistent": round(float(np.mean(ms_b)), 3), "ms_plain": round(float(np.mean(ms_p)), 3)}
+                      "ms_persistent": round(float(np.mean(ms_b)), 3), "ms_plain": round(float(np.mean(ms_p)), 3),
+                      "roofline": roofline(march_bytes(cnt_b, n_pix), float(np.mean(ms_b)), "render_persistent_kernel",
+                                           profile="render_persistent_batch1024"),
+                      "roofline_plain": roofline(march_bytes(cnt_b, n_pix), float(np.mean(ms_p)), "render_image_kernel",
+                                                 launches=int(len(cams)))}
     del buf
     # forward + backward of 65,536 rays on the 512^3 grid
     wsc = synth.make_scene("bwd512")
@@ -411,13 +441,18 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
     ms_fb = time_steps(fwd_bwd, reps, 2, stream, flush)
     ms_tr = time_steps(fused, reps, 2, stream, flush)
     n = pix.shape[0]
+    cnt = rb.render_rays(wsc.cameras, pix, wm, counts=True)["counts"].double().sum(0).cpu().numpy()
+    rl_fb, rl_tr = training_rooflines(cnt, n, float(np.mean(ms_fb)), float(np.mean(ms_tr)), "bwd512")
     out["fwd_bwd"] = {"workload": f"bwd512: {wsc.N}^3 grid, {wsc.occupancy * 100:.1f}% occupied, {n} rays over 8 views",
                       "scene_checksum": wsc.checksum(),
                       "fwd_mrays_s": round(n / (np.mean(ms_f) * 1e-3) / 1e6, 3),
                       "fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3),
                       "fused_train_mrays_s": round(n / (np.mean(ms_tr) * 1e-3) / 1e6, 3),
                       "ms_fwd": round(float(np.mean(ms_f)), 4), "ms_fwd_bwd": round(float(np.mean(ms_fb)), 4),
-                      "ms_fused_train": round(float(np.mean(ms_tr)), 4)}
+                      "ms_fused_train": round(float(np.mean(ms_tr)), 4),
+                      "roofline_fwd": roofline(march_bytes(cnt, n) + 12 * n, float(np.mean(ms_f)), "render_rays_kernel",
+                                               profile="render_rays_bwd512"),
+                      "roofline": rl_fb, "roofline_fused_train": rl_tr}
     # fine-tuning steps (Sec. 5.5): render -> L2 loss -> adjoint -> Adam, all in the library
     ft = renderer.FineTuner(rb, wsc.mlp)
     ms_ft = time_steps(lambda: ft.step(wsc.cameras, pix, tgt), reps, 2, stream, flush)
@@ -439,6 +474,24 @@ def extra_sections(args, r, sc, dev, stream, flush, barrier):
     if not args.no_large:
         out["large"] = large_section(args, dev, stream, flush)
     return out
+
+
+def training_rooflines(cnt, n, ms_fb, ms_tr, tag):
+    """Rooflines of a training step over n listed rays (cnt: column sums of the forward's
+    debug counts). Two-launch form: the ray-list forward (march, 12 B pixel record in, 12 B
+    colour and 48 B per-ray state out) and the adjoint (pixel, dL/dC and the state in; per
+    composited sample the stencil again and the vector atomics into the gradient atlas; one
+    atomic per MLP parameter per CTA). One-launch form (snerg_train_rays): the march, pixel
+    and target in, colour out, and the same adjoint traffic. The adjoint's own march through
+    block entries and density probes is not counted (a lower bound)."""
+    ctas = -(-n // 128)
+    adj = ADJ_BYTES_PER_SAMPLE * cnt[1] + MLP_GRAD_BYTES_PER_CTA * ctas
+    two = (march_bytes(cnt, n) + 12 * n + 48 * n) + (72 * n + adj)
+    one = march_bytes(cnt, n) + 24 * n + adj
+    return (roofline(two, ms_fb, "render_rays_kernel + backward_rays_kernel", profile=f"backward_rays_{tag}",
+                     sources=BWD_SOURCES, launches=2),
+            roofline(one, ms_tr, "backward_rays_kernel<1> (snerg_train_rays)", profile=f"train_rays_{tag}",
+                     sources=BWD_SOURCES))
 
 
 def orbit_section(args, r, sc, dev, stream, flush):
@@ -544,8 +597,7 @@ def large_section(args, dev, stream, flush):
     buf = torch.empty((n_pix, 3), dtype=torch.float32, device=dev)
     reps = max(3, min(args.steps, 10))
     dbg = r.render(sc.cameras, None, counts=True)
-    cnt = dbg["counts"].double().sum(0).cpu().numpy()
-    alg = 4 * cnt[2] + cnt[0] + 64 * cnt[1] + 12 * n_pix
+    alg = march_bytes(dbg["counts"].double().sum(0).cpu().numpy(), n_pix)
     del dbg
     ms_b = time_steps(lambda: r.render(sc.cameras, None, out=buf, persistent=True), reps, 2, stream, flush)
     del buf
@@ -569,17 +621,21 @@ def large_section(args, dev, stream, flush):
     ms_tr = time_steps(lambda: r.train_rays(sc.cameras, pix, mlp, tgt, ga, gm, loss=loss, out=c), reps, 2, stream,
                        flush)
     r.check_status()
-    peak = float(measured_peaks()[0]["hbm_gbs"])
+    cnt_r = r.render_rays(sc.cameras, pix, mlp, counts=True)["counts"].double().sum(0).cpu().numpy()
+    rl_fb, rl_tr = training_rooflines(cnt_r, n, float(np.mean(ms_fb)), float(np.mean(ms_tr)), "shell2048")
     t_b = float(np.mean(ms_b))
     return {"workload": f"shell2048: {sc.N}^3 grid, {sc.B}^3 blocks, {sc.occupancy * 100:.1f}% occupied "
                         f"({sc.nb} blocks), 8 views at 1920x1080 + {n} backward rays",
             "scene_checksum": sc.checksum(),
             "batched_fwd_mrays_s": round(n_pix / (t_b * 1e-3) / 1e6, 3),
             "batched_fwd_ms": round(t_b, 3),
-            "batched_fwd_hbm_frac": round(alg / (t_b * 1e-3) / 1e9 / peak, 4),
+            "batched_fwd_roofline": roofline(alg, t_b, "render_persistent_kernel", profile="render_persistent_shell2048"),
             "rays_fwd_mrays_s": round(n / (np.mean(ms_f) * 1e-3) / 1e6, 3),
             "rays_fwd_bwd_mrays_s": round(n / (np.mean(ms_fb) * 1e-3) / 1e6, 3),
-            "rays_fused_train_mrays_s": round(n / (np.mean(ms_tr) * 1e-3) / 1e6, 3)}
+            "rays_fused_train_mrays_s": round(n / (np.mean(ms_tr) * 1e-3) / 1e6, 3),
+            "rays_fwd_roofline": roofline(march_bytes(cnt_r, n) + 12 * n, float(np.mean(ms_f)), "render_rays_kernel",
+                                          profile="render_rays_shell2048"),
+            "rays_fwd_bwd_roofline": rl_fb, "rays_fused_train_roofline": rl_tr}
 
 
 def cpu_baseline(sc):

@@ -237,6 +237,19 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
             }
         }
     }
+    // the atlas scatter before the CTA's barrier: each ray's second march follows its own
+    // first one instead of waiting for the CTA's slowest first march
+    if (active && grad_atlas) {
+        float gf[7];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gf[c] = sc * (g[c] + gx[c]);     // C = s C_d + residual
+#pragma unroll
+        for (int c = 0; c < 4; ++c) gf[3 + c] = sc * gx[3 + c];
+        // the second pass starts at the first composited sample: nothing before it
+        // contributes (T = 1 and tau = 0 there), so its weights are the first pass's
+        MarchState st2;
+        march<false, true, false, true>(s, r, st2, nullptr, 0, gf, grad_atlas, k_first);
+    }
     if (TRAIN && loss) {
         float v = l2;
 #pragma unroll
@@ -270,17 +283,6 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
             }
             if (acc != 0.0f) atomicAdd(grad_mlp + p, acc);
         }
-    }
-    if (active && grad_atlas) {
-        float gf[7];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) gf[c] = sc * (g[c] + gx[c]);     // C = s C_d + residual
-#pragma unroll
-        for (int c = 0; c < 4; ++c) gf[3 + c] = sc * gx[3 + c];
-        // the second pass starts at the first composited sample: nothing before it
-        // contributes (T = 1 and tau = 0 there), so its weights are the first pass's
-        MarchState st2;
-        march<false, true, false, true>(s, r, st2, nullptr, 0, gf, grad_atlas, k_first);
     }
 }
 

@@ -243,7 +243,11 @@ __device__ __forceinline__ float box_exit(const Ray& r, const float inv_d[3], fl
     }
     const float K = te - r.t0 - 0.5f;
     const float n = ceilf(K);
-    const float fr = n - K;                   // in [0, 1); exact for |K| >= 1 (Sterbenz)
+    // fr in [0, 1). n - K is exact for K >= 1/2 (Sterbenz) and for K <= 0; for K in
+    // (0, 1/2), n = 1 and 1 - K rounds by at most 2^-25, far inside the margin (at least
+    // 4 * 2^-20, four times the bound on the estimate's own error), so the test below
+    // decides the same way.
+    const float fr = n - K;
     if (n >= k + 1.0f && n < kmax && fr >= margin && fr < 1.0f - margin) return n;
     // estimate clamped to [k + 1, kmax] (fminf/fmaxf also map a NaN estimate into range)
     const float ke = fmaxf(fminf(n, kmax), k + 1.0f);

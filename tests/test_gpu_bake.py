@@ -153,10 +153,12 @@ def test_baked_grid_renders_like_the_oracle_bake():
 
 
 def test_bake_paper_scale_sampled():
-    """The 1024^3 grid of 32^3 macroblocks with 64 blobs on a sphere (the bench's bake):
-    48 macroblocks sampled across kept, culled-next-to-kept and random blocks are recomputed
-    one by one by the oracle; kept decisions and contents agree (outside the rounding band),
-    and the slots are numbered in raster order."""
+    """The bench's bake: the 1024^3 grid of 32^3 macroblocks with 64 blobs on a sphere.
+    128 macroblocks -- 64 kept, 32 culled ones with a kept face neighbour (where the
+    tau_alpha decision is closest) and 32 random ones -- are recomputed one by one by the
+    oracle; kept decisions agree outside the tau_alpha ambiguity band, the kept blocks'
+    codes agree outside the rounding band (within one code inside it), and the slots are
+    numbered in raster order."""
     N, B, sigma_max = 1024, 32, 200.0
     G = N // B
     f = synth.analytic_field(1)
@@ -166,14 +168,21 @@ def test_bake_paper_scale_sampled():
     assert (flat[kept] == np.arange(kept.size)).all() and atl_g.shape[0] == kept.size
     assert 0.02 < kept.size / G ** 3 < 0.5
     rng = np.random.default_rng(9)
-    near = np.flatnonzero((flat < 0) & (np.roll(flat, 1) >= 0))
-    sample = np.unique(np.concatenate([rng.choice(kept, 16, replace=False), rng.choice(near, 16, replace=False),
-                                       rng.choice(G ** 3, 16, replace=False)]))
+    occ = ind_g >= 0
+    pad = np.pad(occ, 1)
+    nbr = np.zeros_like(occ)
+    for ax in range(3):
+        for sh in (-1, 1):
+            nbr |= np.roll(pad, sh, axis=ax)[1:-1, 1:-1, 1:-1]
+    near = np.flatnonzero((~occ & nbr).ravel())
+    sample = np.unique(np.concatenate([rng.choice(kept, 64, replace=False), rng.choice(near, 32, replace=False),
+                                       rng.choice(G ** 3, 32, replace=False)]))
     amax, content, raw = oracle.bake_blocks(N, B, BMIN, EXTENT, sigma_max, f["blobs"], f["colors"], f["jitter"],
                                             sample)
     ambiguous = np.abs(amax - TAU) <= 5e-5 * TAU
     assert (((flat[sample] >= 0) == (amax >= TAU)) | ambiguous).all()
     sel = flat[sample] >= 0
+    assert sel.sum() >= 64
     ndiff = _compare_blocks(atl_g[flat[sample][sel]], content[sel], raw[sel])
     assert ndiff <= 1e-4 * content[sel].size + 2
 

@@ -373,6 +373,64 @@ def test_paper_scale_2048_batched_forward_and_backward():
     assert np.abs(gm.cpu().numpy() - rm).max() <= 1e-4 * np.abs(rm).max()
 
 
+def _subscene_for_rays(sc, pix, trace_cap=256):
+    """The blocks that decide the listed rays: every occupied block holding a trilinear
+    corner of one of their composited samples (the nearest voxels of those samples, from
+    the oracle's trace, moved by -1, 0 or +1 voxel per axis). A block outside this set only
+    ever holds samples of these rays whose nearest density code is 0, so emptying it
+    changes nothing they composite. Returns (sub-scene, its blocks' raster indices)."""
+    o = oracle.render_rays(sc, pix, trace_cap=trace_cap)
+    act = o["counts"][:, 1]
+    assert act.max() <= trace_cap
+    N, B = sc.N, sc.B
+    G = N // B
+    vox = np.concatenate([o["trace"][i, :act[i]] for i in range(pix.shape[0])]).astype(np.int64)
+    z, y, x = vox // (N * N), (vox // N) % N, vox % N
+    blocks = np.unique(np.concatenate([
+        (np.clip(z + dz, 0, N - 1) // B * G + np.clip(y + dy, 0, N - 1) // B) * G + np.clip(x + dx, 0, N - 1) // B
+        for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]))
+    ind = np.asarray(sc.ind).reshape(-1)
+    keep = blocks[ind[blocks] >= 0]
+    sub_ind = np.full(G ** 3, -1, np.int32)
+    sub_ind[keep] = np.arange(keep.size, dtype=np.int32)
+    sub = synth.custom_scene(N, B, sub_ind.reshape(np.asarray(sc.ind).shape), sc.atlas[ind[keep]], sc.sigma_max,
+                             sc.mlp, sc.cameras)
+    # the sub-scene renders these rays exactly as the full scene does
+    np.testing.assert_array_equal(oracle.render_rays(sub, pix)["rgb"], o["rgb"])
+    return sub, keep
+
+
+def test_paper_scale_2048_atlas_gradient_subscene():
+    """The atlas gradient of the 2048^3 grid (262,144-ray backward workload; Sec. 5.5),
+    element by element against the FP64 oracle for 8192 of the listed rays. The oracle runs
+    on a sub-scene holding only the blocks those rays composite from (see
+    _subscene_for_rays), so its FP64 gradient array is a few GB instead of 13 GB; the GPU
+    runs on the full grid, and every gradient entry outside those blocks must be 0."""
+    sc = scene("shell2048")
+    bp = sc.extra["pix"][:8192]
+    sub, keep = _subscene_for_rays(sc, bp)
+    gr = np.random.default_rng(25).normal(size=(bp.shape[0], 3)).astype(np.float32)
+    r = renderer.Renderer.from_scene(sc, DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    ga = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=DEV)
+    gm = torch.zeros(883, dtype=torch.float32, device=DEV)
+    r.backward(sc.cameras, torch.from_numpy(bp).to(DEV), w, torch.from_numpy(gr).to(DEV), ga, gm)
+    r.check_status()
+    slots = torch.from_numpy(np.asarray(sc.ind).reshape(-1)[keep].astype(np.int64)).to(DEV)
+    outside = torch.ones(sc.nb, dtype=torch.bool, device=DEV)
+    outside[slots] = False
+    flat = ga.view(sc.nb, -1)
+    assert float(flat.amax(1)[outside].max()) == 0.0 and float(flat.amin(1)[outside].min()) == 0.0
+    got = ga[slots].cpu().numpy()
+    del ga
+    ra, rm = oracle.backward_rays(sub, bp, gr)
+    sa = np.abs(ra).max()
+    assert sa > 0 and (got[..., 0] == 0).all()
+    assert np.abs(got - ra).max() <= 1e-4 * sa
+    assert np.abs(gm.cpu().numpy() - rm).max() <= 1e-4 * np.abs(rm).max()
+    assert keep.size > 500                       # the rays reach many blocks of the grid
+
+
 def test_parameter_weights_match_device_weights():
     """snerg_set_mlp + d_mlp = NULL (weights as kernel parameters) renders what the
     device-weight path renders, for the plain, ray-list and persistent launches."""
