@@ -86,13 +86,20 @@ MLP_GRAD_BYTES_PER_CTA = 883 * 4 * 2      # one atomic per parameter per CTA (re
 
 def roofline(alg_bytes, ms, kernel, profile=None, sources=FWD_SOURCES, launches=1):
     """The roofline object of one timed launch (or `launches` launches per step): counted
-    algorithmic bytes over the mean CUDA-event time, against the measured HBM copy peak."""
+    algorithmic bytes over the mean CUDA-event time, against the measured HBM copy peak.
+    profile: the ncu summary (or a list of (summary, sources), one per launch of the step)
+    whose DRAM bytes give `traffic`."""
     peaks, src = measured_peaks()
     peak = float(peaks["hbm_gbs"])
     achieved = alg_bytes / (ms * 1e-3) / 1e9
+    traffic = None
+    if isinstance(profile, list):
+        parts = [profiled_traffic(p, s) for p, s in profile]
+        traffic = None if any(t is None for t in parts) else sum(parts)
+    elif profile:
+        traffic = profiled_traffic(profile, sources)
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4),
-            "traffic": profiled_traffic(profile, sources) if profile else None,
+            "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"{src} hbm_gbs", "kernel": kernel, "launches_per_step": launches,
             ("algorithmic_bytes_per_launch" if launches == 1 else "algorithmic_bytes_per_step"): int(alg_bytes)}
 
@@ -488,8 +495,9 @@ def training_rooflines(cnt, n, ms_fb, ms_tr, tag):
     adj = ADJ_BYTES_PER_SAMPLE * cnt[1] + MLP_GRAD_BYTES_PER_CTA * ctas
     two = (march_bytes(cnt, n) + 12 * n + 48 * n) + (72 * n + adj)
     one = march_bytes(cnt, n) + 24 * n + adj
-    return (roofline(two, ms_fb, "render_rays_kernel + backward_rays_kernel", profile=f"backward_rays_{tag}",
-                     sources=BWD_SOURCES, launches=2),
+    return (roofline(two, ms_fb, "render_rays_kernel + backward_rays_kernel",
+                     profile=[(f"render_rays_{tag}", FWD_SOURCES), (f"backward_rays_{tag}", BWD_SOURCES)],
+                     launches=2),
             roofline(one, ms_tr, "backward_rays_kernel<1> (snerg_train_rays)", profile=f"train_rays_{tag}",
                      sources=BWD_SOURCES))
 
@@ -669,10 +677,20 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-large", action="store_true", help="skip the 2048^3 section")
+    ap.add_argument("--only", choices=["large"], default=None,
+                    help="run one extra section alone and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     ws, rank, local = dist_setup()
+    if args.only == "large":
+        import torch
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        stream = torch.cuda.current_stream(dev)
+        flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps({"large": large_section(args, dev, stream, lambda: flush_buf.fill_(1))}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
     else:
