@@ -120,7 +120,25 @@ typedef struct {
                               into bands on several streams and copy each band out as soon
                               as it is done. */
     int32_t row_end;
+    int32_t schedule;      /* snerg_render only. 1 = a viewer's tile schedule: this call's
+                              16x8-pixel tiles are launched in the order of the tile costs
+                              (CTA durations) the handle recorded on its last schedule = 1
+                              render of a camera of the same W x H, slowest first, and this
+                              call records its own tile costs for the next one; the first such
+                              call, or a new size, launches in raster order. Consecutive
+                              frames of a moving camera have their slow tiles (rays grazing
+                              surfaces) in nearly the same places, so those start first
+                              instead of at their raster position. The pixels are exactly
+                              those of a raster-order launch. Applies to one camera, all
+                              rows, no debug outputs, not persistent, the deferred model and
+                              at most SNERG_SCHEDULE_MAX_TILES tiles; other calls launch in
+                              raster order. Calls that overlap on the GPU must not both use
+                              it. 0 = raster order. */
 } snerg_render_opts;
+
+/* Largest image (in 16x8-pixel tiles) whose tile costs a handle records (4096 x 2048
+ * pixels). */
+#define SNERG_SCHEDULE_MAX_TILES 65536
 
 /* Largest number of cameras in one snerg_render / ray-list call. */
 #define SNERG_MAX_CAMERAS 256
@@ -131,8 +149,9 @@ typedef struct {
 /* Bytes of device workspace snerg_create needs for `num_blocks` occupied macroblocks;
  * 0 if the description is invalid. The workspace holds the apron-padded device copy of
  * the atlas, the indirection grid, the empty-space distance maps (per octant of the ray
- * direction: one per block, one per stored voxel) and the status word: about
- * 16 (B+2)^3 bytes per block + 35 (N/B)^3 bytes. */
+ * direction: one per block, one per stored voxel), the status word and the tile costs of
+ * the viewer's schedule (snerg_render_opts.schedule): about 16 (B+2)^3 bytes per block
+ * + 35 (N/B)^3 bytes + 16 MiB. */
 size_t snerg_workspace_bytes(const snerg_scene_desc* desc, int64_t num_blocks);
 
 /* Build a scene handle (Sec. 5.1 data structure).

@@ -27,8 +27,13 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-    size_t ind, bdist, btmp, blk, vskip, patlas, total;
+    size_t ind, bdist, btmp, blk, vskip, patlas, sched, total;
 };
+
+// tile schedule (snerg_render_opts.schedule): two sets (the previous frame's and this
+// frame's) of kSchedBuckets counts and kSchedBuckets x kSchedMaxTiles tile lists
+constexpr size_t kSchedCountBytes = 256;
+constexpr size_t kSchedSetBytes = kSchedCountBytes + (size_t)kSchedBuckets * kSchedMaxTiles * 4;
 
 constexpr int kBlockDistCap = 32;   // block-level distances are capped (a smaller box is still empty)
 
@@ -68,7 +73,8 @@ bool make_layout(const snerg_scene_desc* d, int64_t nb, Layout* L) {
     L->blk = align_up(L->btmp + 2 * G3);
     L->vskip = align_up(L->blk + (size_t)nb * 4);
     L->patlas = align_up(L->vskip + 8 * (size_t)nb * P3);    // one voxel plane per octant
-    L->total = align_up(L->patlas + (size_t)nb * P3 * 8);
+    L->sched = align_up(L->patlas + (size_t)nb * P3 * 8);
+    L->total = align_up(L->sched + 2 * kSchedSetBytes);
     return true;
 }
 
@@ -118,6 +124,11 @@ struct snerg_scene {
     PersistentConfig last{0, 0, 0, 0, 0};
     MlpWeights host_w;        // snerg_set_mlp: weights in the transposed kernel layout
     bool has_w = false;
+    // tile schedule: the image size whose tile costs set `sched_set` holds (valid after the
+    // first schedule = 1 render of that size)
+    int32_t sched_w = 0, sched_h = 0;
+    int sched_set = 0;
+    bool sched_valid = false;
     std::vector<cudaStream_t> band_streams;   // snerg_render_to_host: one per band
     std::vector<cudaEvent_t> band_done;
     cudaEvent_t band_fork = nullptr;
@@ -423,7 +434,35 @@ extern "C" snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, i
         if (rows) return SNERG_E_UNSUPPORTED;
         return render_persistent(h, cams, n_cams, d_mlp, pw, d_rgb, opts, st);
     }
+    if (opts && (opts->schedule < 0 || opts->schedule > 1)) return SNERG_E_INVAL;
     const DebugOut dbg = make_dbg(opts);
+    const int tiles = ((cams[0].W + 15) / 16) * ((cams[0].H + 7) / 8);
+    if (opts && opts->schedule == 1 && n_cams == 1 && !rows && !opts_debug(opts) &&
+        !(h->desc.flags & SNERG_FLAG_PER_SAMPLE_MLP) && tiles <= kSchedMaxTiles) {
+        // the previous frame's buckets (if they describe an image of this size) give the
+        // order; this frame's go to the other set, whose counts start at zero
+        Layout L;
+        make_layout(&h->desc, h->nb, &L);
+        uint8_t* set[2] = {h->ws + L.sched, h->ws + L.sched + kSchedSetBytes};
+        const bool use = h->sched_valid && h->sched_w == cams[0].W && h->sched_h == cams[0].H;
+        uint8_t* rd = set[h->sched_set];
+        uint8_t* wr = set[h->sched_set ^ 1];
+        SchedArgs sa;
+        sa.rd_count = use ? (const int32_t*)rd : nullptr;
+        sa.rd_list = (const int32_t*)(rd + kSchedCountBytes);
+        sa.wr_count = (int32_t*)wr;
+        sa.wr_list = (int32_t*)(wr + kSchedCountBytes);
+        sa.cap = kSchedMaxTiles;
+        cudaError_t e = cudaMemsetAsync(wr, 0, kSchedBuckets * sizeof(int32_t), st);
+        if (e == cudaSuccess) e = launch_render_image(h->ds, cams[0], d_mlp, pw, d_rgb, dbg, st, 0, cams[0].H, &sa);
+        if (e != cudaSuccess) return SNERG_E_CUDA;
+        h->launches++;
+        h->sched_set ^= 1;
+        h->sched_w = cams[0].W;
+        h->sched_h = cams[0].H;
+        h->sched_valid = true;
+        return SNERG_OK;
+    }
     for (int i = 0; i < n_cams; ++i) {
         if (cams[i].W == 0 || cams[i].H == 0) continue;
         const int r0 = rows ? opts->row_begin : 0, r1 = rows ? opts->row_end : cams[i].H;

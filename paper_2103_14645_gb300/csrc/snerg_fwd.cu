@@ -21,23 +21,61 @@ struct ImageTile {
     static constexpr int TW = 8 * WX, TH = 4 * WY;  // CTA tile in pixels
 };
 
-template <bool DBG, bool PW, int NW, bool PS>
-__global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const DevScene s, const snerg_camera cam,
-                                                                        const float* __restrict__ mlp,
-                                                                        const __grid_constant__ MlpWeights pw,
-                                                                        float* __restrict__ rgb, const DebugOut dbg,
-                                                                        int row0, int row1) {
-    __shared__ __align__(16) float sW[PW ? 4 : kNParam + 1];
-    if (!PW) {
-        load_mlp_smem_t(sW, mlp);
-        __syncthreads();
+// SCHED: the CTA's tile comes from the previous frame's cost buckets (heaviest bucket
+// first; launch index i is the i-th tile in that order), and the CTA records its own
+// duration in this frame's buckets when all its warps are done. The pixels it renders are
+// those of the tile, so the image does not depend on the order.
+template <bool SCHED>
+__device__ __forceinline__ int sched_tile(const SchedArgs& sch, int item, unsigned long long* t0) {
+    __shared__ int s_tile;
+    if (SCHED && threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0) {
+            s_tile = item;                      // raster order unless a bucket holds it
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            *t0 = t;
+        }
+        __syncwarp();
+        if (sch.rd_count) {
+            const int b = kSchedBuckets - 1 - lane;      // lane 0: the heaviest bucket
+            const int c = __ldg(sch.rd_count + b);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int excl = incl - c;
+            // the buckets are used only when they hold exactly this launch's tiles
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total == (int)(gridDim.x * gridDim.y) && item >= excl && item < incl && item - excl < sch.cap)
+                s_tile = __ldg(sch.rd_list + (size_t)b * sch.cap + (item - excl));
+        }
     }
-    const MlpWeights* pwp = PW ? &pw : nullptr;
-    using T = ImageTile<NW>;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = blockIdx.x * T::TW + (warp % T::WX) * 8 + (lane & 7);
-    const int py = row0 + blockIdx.y * T::TH + (warp / T::WX) * 4 + (lane >> 3);
-    if (px >= cam.W || py >= row1) return;
+    if (SCHED) __syncthreads();
+    return SCHED ? s_tile : item;
+}
+
+template <bool SCHED>
+__device__ __forceinline__ void sched_record(const SchedArgs& sch, int tile, const unsigned long long* t0) {
+    if (!SCHED) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        const float ns = (float)(t1 - *t0);
+        const int b = min(max((int)(3.0f * __log2f(fmaxf(ns, 1.0f) * (1.0f / 250.0f))), 0), kSchedBuckets - 1);
+        const int pos = atomicAdd(sch.wr_count + b, 1);
+        if (pos < sch.cap) sch.wr_list[(size_t)b * sch.cap + pos] = tile;
+    }
+}
+
+// one pixel of render_image_kernel: march, MLP, store (and the debug outputs)
+template <bool DBG, bool PS>
+__device__ __forceinline__ void image_pixel(const DevScene& s, const snerg_camera& cam, const float* sW,
+                                            const MlpWeights* pwp, float* __restrict__ rgb, const DebugOut& dbg,
+                                            int px, int py) {
     const Ray r = make_ray(s, cam, px, py);
     const int64_t pix = cam.out_offset + (int64_t)py * cam.W + px;
     MarchState st;
@@ -62,6 +100,35 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const De
             dbg.counts[pix * 4 + 2] = st.blocks;
             dbg.counts[pix * 4 + 3] = st.active > 0 ? k_first : -1;
         }
+    }
+}
+
+template <bool DBG, bool PW, int NW, bool PS, bool SCHED = false>
+__global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const DevScene s, const snerg_camera cam,
+                                                                        const float* __restrict__ mlp,
+                                                                        const __grid_constant__ MlpWeights pw,
+                                                                        float* __restrict__ rgb, const DebugOut dbg,
+                                                                        int row0, int row1, const SchedArgs sch) {
+    __shared__ __align__(16) float sW[PW ? 4 : kNParam + 1];
+    if (!PW) {
+        load_mlp_smem_t(sW, mlp);
+        __syncthreads();
+    }
+    const MlpWeights* pwp = PW ? &pw : nullptr;
+    using T = ImageTile<NW>;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (SCHED) {
+        __shared__ unsigned long long s_t0;
+        const int tile = sched_tile<true>(sch, (int)(blockIdx.y * gridDim.x + blockIdx.x), &s_t0);
+        const int px = (tile % (int)gridDim.x) * T::TW + (warp % T::WX) * 8 + (lane & 7);
+        const int py = row0 + (tile / (int)gridDim.x) * T::TH + (warp / T::WX) * 4 + (lane >> 3);
+        if (px < cam.W && py < row1) image_pixel<DBG, PS>(s, cam, sW, pwp, rgb, dbg, px, py);
+        sched_record<true>(sch, tile, &s_t0);
+    } else {
+        const int px = blockIdx.x * T::TW + (warp % T::WX) * 8 + (lane & 7);
+        const int py = row0 + blockIdx.y * T::TH + (warp / T::WX) * 4 + (lane >> 3);
+        if (px >= cam.W || py >= row1) return;
+        image_pixel<DBG, PS>(s, cam, sW, pwp, rgb, dbg, px, py);
     }
 }
 
@@ -172,29 +239,38 @@ static const MlpWeights& no_weights() {
 
 template <bool PS>
 static void image_launch(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
-                         float* rgb, const DebugOut& dbg, cudaStream_t st, int row0, int row1) {
+                         float* rgb, const DebugOut& dbg, cudaStream_t st, int row0, int row1, const SchedArgs* sch) {
     using T = ImageTile<kImageWarps>;
     dim3 grid((cam.W + T::TW - 1) / T::TW, (row1 - row0 + T::TH - 1) / T::TH);
     const int nt = 32 * kImageWarps;
     const bool d = dbg.aux || dbg.counts || dbg.trace;
     const MlpWeights& w = pw ? *pw : no_weights();
+    const SchedArgs none{nullptr, nullptr, nullptr, nullptr, 0};
+    if (!PS && !d && sch) {
+        if (pw) render_image_kernel<false, true, kImageWarps, false, true><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg,
+                                                                                              row0, row1, *sch);
+        else render_image_kernel<false, false, kImageWarps, false, true><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg,
+                                                                                                row0, row1, *sch);
+        return;
+    }
     if (pw) {
-        if (d) render_image_kernel<true, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1);
-        else render_image_kernel<false, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1);
+        if (d) render_image_kernel<true, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1, none);
+        else render_image_kernel<false, true, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1, none);
     } else {
-        if (d) render_image_kernel<true, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1);
-        else render_image_kernel<false, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1);
+        if (d) render_image_kernel<true, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1, none);
+        else render_image_kernel<false, false, kImageWarps, PS><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg, row0, row1, none);
     }
 }
 
 // rows [row0, row1) of the camera (clamped to [0, H]); all rows when row1 <= row0 after clamping
 cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
-                                float* rgb, const DebugOut& dbg, cudaStream_t st, int row0, int row1) {
+                                float* rgb, const DebugOut& dbg, cudaStream_t st, int row0, int row1,
+                                const SchedArgs* sch) {
     row0 = max(row0, 0);
     row1 = min(row1, cam.H);
     if (cam.W <= 0 || row1 <= row0) return cudaSuccess;
-    if (s.flags & SNERG_FLAG_PER_SAMPLE_MLP) image_launch<true>(s, cam, mlp, pw, rgb, dbg, st, row0, row1);
-    else image_launch<false>(s, cam, mlp, pw, rgb, dbg, st, row0, row1);
+    if (s.flags & SNERG_FLAG_PER_SAMPLE_MLP) image_launch<true>(s, cam, mlp, pw, rgb, dbg, st, row0, row1, nullptr);
+    else image_launch<false>(s, cam, mlp, pw, rgb, dbg, st, row0, row1, sch);
     return cudaGetLastError();
 }
 

@@ -871,9 +871,25 @@ struct DebugOut {
     int32_t trace_cap;
 };
 
+// Tile schedule from the previous frame (snerg_render_opts.schedule): the image's 16x8
+// tiles in cost buckets, bucket = 3 log2(the tile's CTA duration / 250 ns) clamped to
+// [0, 32). Bucket b's tiles are list[b * cap + 0 .. count[b]).
+constexpr int kSchedBuckets = 32;
+constexpr int kSchedMaxTiles = SNERG_SCHEDULE_MAX_TILES;
+struct SchedArgs {
+    const int32_t* rd_count;   // the previous frame's buckets (nullptr: raster order)
+    const int32_t* rd_list;
+    int32_t* wr_count;         // this frame's buckets (counts zeroed before the launch)
+    int32_t* wr_list;
+    int32_t cap;               // list capacity per bucket (>= the image's tiles)
+};
+
 // pw: weights as a kernel parameter (nullptr: read them from `mlp` in device memory)
+// sch: nullable; with it the launch takes its tile order from the previous frame's
+// buckets and records its own tile costs (deferred model, all rows, no debug outputs)
 cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, const float* mlp, const MlpWeights* pw,
-                                float* rgb, const DebugOut& dbg, cudaStream_t st, int row0, int row1);
+                                float* rgb, const DebugOut& dbg, cudaStream_t st, int row0, int row1,
+                                const SchedArgs* sch = nullptr);
 cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
                                int64_t n, const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg,
                                cudaStream_t st);

@@ -52,7 +52,7 @@ class RenderOpts(ctypes.Structure):
     _fields_ = [("d_aux", ctypes.c_void_p), ("d_counts", ctypes.c_void_p), ("d_trace", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_int32), ("persistent", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("tile_h", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("row_begin", ctypes.c_int32),
-                ("row_end", ctypes.c_int32)]
+                ("row_end", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
 class BakeField(ctypes.Structure):
@@ -249,11 +249,15 @@ class Renderer:
         return o, out
 
     def render(self, cams, mlp: torch.Tensor | None, out: torch.Tensor | None = None, aux=False, counts=False,
-               trace_cap: int = 0, persistent=False, tile=None, ctas_per_sm: int = 0, rows=None):
+               trace_cap: int = 0, persistent=False, tile=None, ctas_per_sm: int = 0, rows=None,
+               schedule: bool = False):
         """Render every pixel of the cameras into out [pixels, 3] (packed by out_offset), a
         device tensor or a pinned host tensor (written by the kernels through the mapping).
         mlp: device weights, or None for the weights stored with set_mlp.
         rows: (begin, end) renders only those image rows of every camera.
+        schedule: launch the tiles in the order of the costs this handle recorded on its last
+        scheduled render of an image of the same size (a viewer's consecutive frames), and
+        record this render's costs (snerg_render_opts.schedule; one camera only).
         Returns out, or a dict with 'rgb' and the requested debug outputs."""
         c = _cams(cams)
         if mlp is not None:
@@ -273,6 +277,7 @@ class Renderer:
         o, extra = self._opts(n_pix, aux, counts, trace_cap, persistent, tile, ctas_per_sm)
         if rows is not None:
             o.row_begin, o.row_end = int(rows[0]), int(rows[1])
+        o.schedule = 1 if schedule else 0
         code = self.lib.snerg_render(self.handle, c.ctypes.data, c.shape[0], _ptr(mlp), _ptr(out),
                                      ctypes.byref(o), _stream(self.device))
         _check(code, "snerg_render")

@@ -431,6 +431,35 @@ def test_paper_scale_2048_atlas_gradient_subscene():
     assert keep.size > 500                       # the rays reach many blocks of the grid
 
 
+def test_tile_schedule_reproduces_raster_renders():
+    """schedule=True launches each frame's tiles in the cost order recorded on the previous
+    scheduled frame of the same size (a viewer's consecutive frames); the pixels must be
+    those of a raster-order launch, bit for bit: consecutive orbit frames, a frame of
+    another size in between (its own order), back to the first size, both weight paths,
+    and the 800x800 view of the 1024^3 grid."""
+    import math
+    for name, size, frames in (("gauss64", (150, 110), 5), ("shell1024", (800, 800), 3)):
+        sc = scene(name)
+        r = renderer.Renderer.from_scene(sc, DEV)
+        r.set_mlp(sc.mlp)
+        w = torch.from_numpy(sc.mlp).to(DEV)
+        cams = []
+        for i in range(frames):
+            az = 0.3 + 0.04 * i
+            pos = synth.CAM_RADIUS * np.array([math.cos(0.35) * math.cos(az), math.cos(0.35) * math.sin(az),
+                                               math.sin(0.35)])
+            cams.append(np.asarray([synth.look_at_camera(pos, (0.0, 0.0, 0.0), size[0], size[1], 39.0)]))
+        other = np.asarray([synth.look_at_camera(synth.CAM_RADIUS * np.array([0.0, 1.0, 0.2]), (0.0, 0.0, 0.0),
+                                                 61, 37, 39.0)])
+        seq = cams[:2] + [other] + cams[2:] + [other]
+        for k, cam in enumerate(seq):
+            mlp = w if k % 2 else None
+            want = r.render(cam, mlp).cpu().numpy()
+            got = r.render(cam, mlp, schedule=True).cpu().numpy()
+            np.testing.assert_array_equal(got, want)
+        r.check_status()
+
+
 def test_parameter_weights_match_device_weights():
     """snerg_set_mlp + d_mlp = NULL (weights as kernel parameters) renders what the
     device-weight path renders, for the plain, ray-list and persistent launches."""
