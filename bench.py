@@ -310,6 +310,11 @@ def run_ours(args, ws, rank, local):
     t_max = reduce_max(t_step, dev)
     value = whole_job_mrays(ws, n_rays, t_max)
 
+    # side figure (not the headline): the viewer's tile schedule on this view -- each step's
+    # tiles ordered by the costs recorded on the step before, which renders the same view
+    r.render(cams, mlp, out=out, schedule=True)
+    ms_sched = time_steps(lambda: r.render(cams, mlp, out=out, schedule=True), args.steps, args.warmup, stream, flush)
+
     # end to end through the public API with host buffers: camera record in, image out
     host_out = torch.empty((n_rays, 3), dtype=torch.float32, pin_memory=True)
 
@@ -367,6 +372,10 @@ def run_ours(args, ws, rank, local):
                    "l2": "flushed before every timed step (256 MiB write)",
                    "launch": "persistent kernel, CUDA-graph replay" if best == "persistent" else "plain (one launch per view)"},
         "launch_modes_ms": {m: round(v[0], 4) for m, v in modes.items()},
+        "viewer_schedule": {"ms_per_frame": round(float(np.mean(ms_sched)), 4),
+                            "mrays_s": round(n_rays / (float(np.mean(ms_sched)) * 1e-3) / 1e6, 3),
+                            "note": "tiles ordered by the costs of the previous render, which is the same view; "
+                                    "not the headline (see orbit.scheduled_* for consecutive different views)"},
         "frames_per_s": round(1e3 / t_max, 2),
         "roofline": rl,
         "e2e": {"value": round(e2e, 3), "unit": "Mrays/s", "h2d_bytes_per_step": 80 * len(cams),
