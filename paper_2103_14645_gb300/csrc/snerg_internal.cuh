@@ -522,6 +522,23 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 for (int c = 0; c < 8; ++c)
                     tw[c] = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
                 const int B3 = B * B * B;
+                // a stencil inside this block (lower corner at padded coordinate 1 .. B-1 on
+                // every axis) has all eight corners in its own slot: no indirection reads
+                const float ex = fl[0] - ox, ey = fl[1] - oy, ez = fl[2] - oz;
+                const float Bm = (float)(B - 1);
+                if (ex >= 1.0f && ex <= Bm && ey >= 1.0f && ey <= Bm && ez >= 1.0f && ez <= Bm) {
+                    float* g0 = grad_atlas +
+                                ((size_t)slot * B3 + (((int)ez - 1) * B + ((int)ey - 1)) * B + ((int)ex - 1)) * 8;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        float* gp = g0 + ((((c >> 2) & 1) * B + ((c >> 1) & 1)) * B + (c & 1)) * 8;
+                        const float w = wk * tw[c];
+                        atomicAdd(reinterpret_cast<float4*>(gp),
+                                  make_float4(0.0f, w * gfeat[0], w * gfeat[1], w * gfeat[2]));
+                        atomicAdd(reinterpret_cast<float4*>(gp + 4),
+                                  make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
+                    }
+                } else {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int X = min(max((int)fl[0] + (c & 1), 0), N - 1);
@@ -536,6 +553,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                               make_float4(0.0f, w * gfeat[0], w * gfeat[1], w * gfeat[2]));
                     atomicAdd(reinterpret_cast<float4*>(gp + 4),
                               make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
+                }
                 }
             }
             if (saturated) {
