@@ -140,7 +140,10 @@ typedef struct {
  * pixels). */
 #define SNERG_SCHEDULE_MAX_TILES 65536
 
-/* Largest number of cameras in one snerg_render / ray-list call. */
+/* Largest number of cameras in one ray-list call (snerg_render_rays, snerg_render_backward,
+ * snerg_train_rays, snerg_render_rays_noalloc: a ray may name any of them) and in one
+ * persistent launch. snerg_render and snerg_render_to_host take any number; a persistent
+ * render of more cameras runs as consecutive persistent launches of up to this many. */
 #define SNERG_MAX_CAMERAS 256
 /* Number of MLP parameters: W1[16][34], b1[16], W2[16][16], b2[16], W3[3][16], b3[3]
  * (row-major, out x in), float32 (Eq. 7; "2 layers with 16 channels", Sec. 4.2). */
@@ -177,7 +180,7 @@ snerg_status snerg_create(const snerg_scene_desc* desc, const int32_t* d_indirec
 snerg_status snerg_set_mlp(snerg_handle h, const float* mlp);
 
 /* Render every pixel of n_cams cameras (Sec. 5.2 and App. A; Eqs. 2, 5-7).
- *   cams   : HOST array of n_cams (1..SNERG_MAX_CAMERAS) cameras, W, H >= 0.
+ *   cams   : HOST array of n_cams >= 1 cameras, W, H >= 0.
  *   d_mlp  : float32 [SNERG_MLP_PARAMS] view-dependence MLP weights in device memory,
  *            or NULL to use the weights stored with snerg_set_mlp (SNERG_E_INVAL if
  *            none were stored).

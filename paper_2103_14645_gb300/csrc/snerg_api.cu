@@ -417,7 +417,7 @@ static snerg_status render_persistent(snerg_scene* h, const snerg_camera* cams, 
 
 extern "C" snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, int32_t n_cams, const float* d_mlp,
                                      float* d_rgb, const snerg_render_opts* opts, void* stream) {
-    if (!h || !cams || n_cams < 1 || n_cams > kMaxCams) return SNERG_E_INVAL;
+    if (!h || !cams || n_cams < 1) return SNERG_E_INVAL;
     int64_t pixels = 0;
     for (int i = 0; i < n_cams; ++i) {
         if (!camera_ok(cams[i])) return SNERG_E_INVAL;
@@ -432,7 +432,14 @@ extern "C" snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, i
     if (opts && opts->persistent && !opts_debug(opts)) {
         if (h->desc.flags & SNERG_FLAG_PER_SAMPLE_MLP) return SNERG_E_UNSUPPORTED;
         if (rows) return SNERG_E_UNSUPPORTED;
-        return render_persistent(h, cams, n_cams, d_mlp, pw, d_rgb, opts, st);
+        // the camera table of one persistent launch holds kMaxCams cameras; a larger batch
+        // runs as consecutive launches (each camera's pixels go to its own out_offset)
+        for (int c0 = 0; c0 < n_cams; c0 += kMaxCams) {
+            const snerg_status e = render_persistent(h, cams + c0, std::min(kMaxCams, n_cams - c0), d_mlp, pw, d_rgb,
+                                                     opts, st);
+            if (e != SNERG_OK) return e;
+        }
+        return SNERG_OK;
     }
     if (opts && (opts->schedule < 0 || opts->schedule > 1)) return SNERG_E_INVAL;
     const DebugOut dbg = make_dbg(opts);
@@ -479,7 +486,7 @@ constexpr int kMaxBands = 16;
 extern "C" snerg_status snerg_render_to_host(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
                                              const float* d_mlp, float* d_rgb, float* h_rgb, int32_t n_bands,
                                              void* stream) {
-    if (!h || !cams || n_cams < 1 || n_cams > kMaxCams || n_bands < 1 || n_bands > kMaxBands) return SNERG_E_INVAL;
+    if (!h || !cams || n_cams < 1 || n_bands < 1 || n_bands > kMaxBands) return SNERG_E_INVAL;
     int64_t pixels = 0;
     int Hmax = 0;
     for (int i = 0; i < n_cams; ++i) {

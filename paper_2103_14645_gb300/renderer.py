@@ -136,10 +136,11 @@ def _stream(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
 
-def _cams(cams) -> np.ndarray:
+def _cams(cams, limit: bool = True) -> np.ndarray:
+    """Cameras as the ABI's records; ray-list calls take at most MAX_CAMERAS (limit)."""
     c = np.ascontiguousarray(cams, dtype=synth.CAMERA_DTYPE).reshape(-1)
-    if not 1 <= c.shape[0] <= MAX_CAMERAS:
-        raise ValueError(f"1..{MAX_CAMERAS} cameras per call, got {c.shape[0]}")
+    if c.shape[0] < 1 or (limit and c.shape[0] > MAX_CAMERAS):
+        raise ValueError(f"1..{MAX_CAMERAS if limit else 'any'} cameras per call, got {c.shape[0]}")
     return c
 
 
@@ -259,7 +260,7 @@ class Renderer:
         scheduled render of an image of the same size (a viewer's consecutive frames), and
         record this render's costs (snerg_render_opts.schedule; one camera only).
         Returns out, or a dict with 'rgb' and the requested debug outputs."""
-        c = _cams(cams)
+        c = _cams(cams, limit=False)
         if mlp is not None:
             _require_cuda(mlp, "mlp", torch.float32)
         n_pix = int(max((int(x["out_offset"]) + int(x["W"]) * int(x["H"]) for x in c), default=0))
@@ -294,7 +295,7 @@ class Renderer:
         device image `out` (allocated if None) on the library's side streams, each copied out
         as soon as it is done. Enqueued after the current stream's work; host_out is complete
         once the current stream is synchronised."""
-        c = _cams(cams)
+        c = _cams(cams, limit=False)
         if host_out.device.type != "cpu" or host_out.dtype != torch.float32 or not host_out.is_contiguous():
             raise ValueError("host_out must be a contiguous float32 CPU tensor")
         if mlp is not None:

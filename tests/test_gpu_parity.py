@@ -139,6 +139,29 @@ def test_max_camera_count():
     np.testing.assert_array_equal(p["rgb"], g["rgb"])
 
 
+def test_more_cameras_than_one_launch_holds():
+    """snerg_render takes any number of cameras: 600 (more than two persistent launches'
+    camera tables) render as one call, plain and persistent (consecutive launches of at
+    most SNERG_MAX_CAMERAS), against the oracle; ray-list calls still reject more."""
+    sc = scene("tiny")
+    n = 2 * renderer.MAX_CAMERAS + 88
+    cams = synth.orbit_cameras(np.random.default_rng(10), [(6, 5), (3, 7)] * (n // 2), synth.CAM_RADIUS)
+    g, r = gpu_render(sc, cams=cams, counts=True)
+    o = oracle_all(sc, cams=cams)
+    np.testing.assert_array_equal(g["counts"][:, :2], o["counts"])
+    assert np.abs(g["rgb"] - o["rgb"]).max() <= TOL
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    p = r.render(cams, w, persistent=True).cpu().numpy()
+    r.check_status()
+    np.testing.assert_array_equal(p, g["rgb"])
+    host = torch.empty((synth.all_pixels(cams).shape[0], 3), dtype=torch.float32, pin_memory=True)
+    r.render_to_host(cams, host, w)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host.numpy(), g["rgb"])
+    with pytest.raises(ValueError):
+        r.render_rays(cams, torch.zeros((1, 3), dtype=torch.int32, device=DEV), w)
+
+
 # --------------------------------------------------------------------------------------
 # closed forms and degenerate cases on the GPU
 # --------------------------------------------------------------------------------------
