@@ -46,7 +46,10 @@ typedef enum {
     SNERG_E_NOMEM = 2,        /* caller-provided buffer smaller than required */
     SNERG_E_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
     SNERG_E_STEP_LIMIT = 4,   /* device: a ray reached its lattice cap (desc.max_steps) */
-    SNERG_E_UNSUPPORTED = 5   /* request outside the compiled limits */
+    SNERG_E_UNSUPPORTED = 5,  /* request outside the compiled limits */
+    SNERG_E_DEVICE_FAULT = 6  /* snerg_last_status: the stream's context took a sticky device
+                                 fault (illegal address or instruction, misaligned access,
+                                 failed launch); the CUDA context must be recreated */
 } snerg_status;
 
 typedef struct snerg_scene* snerg_handle;
@@ -377,8 +380,9 @@ snerg_status snerg_bake(const snerg_scene_desc* desc, const snerg_bake_field* fi
                         void* d_workspace, size_t ws_bytes, int64_t* num_blocks, void* stream);
 
 /* SYNCHRONISES `stream`, returns and clears the device status word (SNERG_OK or the
- * first device error recorded since the last call), or SNERG_E_CUDA if the stream
- * reports an asynchronous CUDA error. */
+ * first device error recorded since the last call); SNERG_E_DEVICE_FAULT if the stream
+ * reports a sticky device fault (the context is unusable afterwards), SNERG_E_CUDA for
+ * any other asynchronous CUDA error. */
 snerg_status snerg_last_status(snerg_handle h, void* stream);
 
 /* Number of kernels the library launched through this handle since creation. */

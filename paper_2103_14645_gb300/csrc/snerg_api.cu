@@ -617,11 +617,30 @@ extern "C" snerg_status snerg_train_rays(snerg_handle h, const snerg_camera* cam
     return SNERG_OK;
 }
 
+// the CUDA errors that leave the context unusable (a fault in a kernel)
+static bool sticky_fault(cudaError_t e) {
+    switch (e) {
+        case cudaErrorIllegalAddress:
+        case cudaErrorIllegalInstruction:
+        case cudaErrorMisalignedAddress:
+        case cudaErrorInvalidAddressSpace:
+        case cudaErrorInvalidPc:
+        case cudaErrorHardwareStackError:
+        case cudaErrorLaunchFailure:
+        case cudaErrorAssert:
+        case cudaErrorLaunchTimeout:
+            return true;
+        default:
+            return false;
+    }
+}
+
 extern "C" snerg_status snerg_last_status(snerg_handle h, void* stream) {
     if (!h) return SNERG_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     int32_t v = 0;
     cudaError_t e = cudaStreamSynchronize(st);
+    if (sticky_fault(e)) return SNERG_E_DEVICE_FAULT;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&v, h->hdr + kHdrStatus, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->hdr + kHdrStatus, 0, 4, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -680,6 +699,7 @@ extern "C" const char* snerg_status_str(snerg_status s) {
         case SNERG_E_CUDA: return "CUDA error";
         case SNERG_E_STEP_LIMIT: return "a ray exceeded its iteration cap";
         case SNERG_E_UNSUPPORTED: return "unsupported";
+        case SNERG_E_DEVICE_FAULT: return "device fault";
     }
     return "unknown status";
 }

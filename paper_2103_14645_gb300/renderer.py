@@ -25,7 +25,7 @@ MAX_CAMERAS = 256
 AUX_CH = 8
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "CUDA error",
-          4: "a ray exceeded its iteration cap", 5: "unsupported"}
+          4: "a ray exceeded its iteration cap", 5: "unsupported", 6: "device fault"}
 
 EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_render_rays",
             "snerg_render_backward", "snerg_last_status", "snerg_launch_count",
