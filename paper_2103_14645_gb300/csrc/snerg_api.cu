@@ -32,7 +32,8 @@ struct Layout {
 
 // tile schedule (snerg_render_opts.schedule): two sets (the previous frame's and this
 // frame's) of kSchedBuckets counts and kSchedBuckets x kSchedMaxTiles tile lists
-constexpr size_t kSchedCountBytes = 256;
+constexpr size_t kSchedCountBytes = 4096;            // a set's header: kSchedHdrWords int32 words
+static_assert(kSchedHdrWords * 4 <= kSchedCountBytes, "schedule header");
 constexpr size_t kSchedSetBytes = kSchedCountBytes + (size_t)kSchedBuckets * kSchedMaxTiles * 4;
 
 constexpr int kBlockDistCap = 32;   // block-level distances are capped (a smaller box is still empty)
@@ -460,7 +461,11 @@ extern "C" snerg_status snerg_render(snerg_handle h, const snerg_camera* cams, i
         sa.wr_count = (int32_t*)wr;
         sa.wr_list = (int32_t*)(wr + kSchedCountBytes);
         sa.cap = kSchedMaxTiles;
-        cudaError_t e = cudaMemsetAsync(wr, 0, kSchedBuckets * sizeof(int32_t), st);
+        sa.nt = tiles;
+        sa.tiles_x = (cams[0].W + 15) / 16;
+        // sparse slots only with a previous frame to choose the slow tiles from
+        sa.smax = use ? std::min(kSchedMaxSparse, std::max(1, tiles / 8)) : 0;
+        cudaError_t e = cudaMemsetAsync(wr, 0, kSchedCountBytes, st);
         if (e == cudaSuccess) e = launch_render_image(h->ds, cams[0], d_mlp, pw, d_rgb, dbg, st, 0, cams[0].H, &sa);
         if (e != cudaSuccess) return SNERG_E_CUDA;
         h->launches++;

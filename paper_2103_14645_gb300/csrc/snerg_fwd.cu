@@ -21,53 +21,101 @@ struct ImageTile {
     static constexpr int TW = 8 * WX, TH = 4 * WY;  // CTA tile in pixels
 };
 
-// SCHED: the CTA's tile comes from the previous frame's cost buckets (heaviest bucket
-// first; launch index i is the i-th tile in that order), and the CTA records its own
-// duration in this frame's buckets when all its warps are done. The pixels it renders are
-// those of the tile, so the image does not depend on the order.
-template <bool SCHED>
-__device__ __forceinline__ int sched_tile(const SchedArgs& sch, int item, unsigned long long* t0) {
-    __shared__ int s_tile;
-    if (SCHED && threadIdx.x < 32) {
+// SCHED: the launch's CTAs take the image's tiles in the order of the previous frame's
+// cost buckets (slowest first). The slowest tiles -- those whose recorded cost is at least
+// kSchedSparseFrac of the previous frame's time, at most smax of them -- are rendered
+// sparsely: four CTAs per tile, each CTA two of its eight rows, 8 rays per warp, so that
+// their long chains of dependent loads run with less divergence beside them. Launch index
+// c < 4 smax: quarter c % 4 of sparse tile c / 4 (idle if there are fewer); c >= 4 smax:
+// the next tile in order, rendered as usual. The pixels of every tile are rendered once,
+// whatever the order and mapping. Each CTA records its duration when all its warps are
+// done (a sparse tile by its last quarter to finish, as its slowest quarter times
+// kSchedSparseGain: about its dense cost, so that it stays sparse while it stays slow) and
+// the launch's start and end. The grid is
+// nt + 4 smax CTAs: 4 smax sparse slots (S <= smax used), then nt dense slots for the tiles
+// S .. nt - 1 of the order (the last S of them idle).
+struct SchedSlot {
+    int tile;       // -1: idle
+    int quarter;    // -1: dense
+};
+
+__device__ __forceinline__ SchedSlot sched_map(const SchedArgs& sch, int c, unsigned long long* t0) {
+    __shared__ SchedSlot s_slot;
+    if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         if (lane == 0) {
-            s_tile = item;                      // raster order unless a bucket holds it
             unsigned long long t;
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
             *t0 = t;
         }
-        __syncwarp();
+        int incl = 0, c_b = 0, S = 0;
+        bool use = false;
+        const int b = kSchedBuckets - 1 - lane;          // lane 0: the slowest bucket
         if (sch.rd_count) {
-            const int b = kSchedBuckets - 1 - lane;      // lane 0: the heaviest bucket
-            const int c = __ldg(sch.rd_count + b);
-            int incl = c;
+            c_b = __ldg(sch.rd_count + b);
+            incl = c_b;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += v;
             }
-            const int excl = incl - c;
             // the buckets are used only when they hold exactly this launch's tiles
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            if (total == (int)(gridDim.x * gridDim.y) && item >= excl && item < incl && item - excl < sch.cap)
-                s_tile = __ldg(sch.rd_list + (size_t)b * sch.cap + (item - excl));
+            use = __shfl_sync(0xffffffffu, incl, 31) == sch.nt;
+            if (use && sch.smax > 0) {
+                const unsigned long long* tw = reinterpret_cast<const unsigned long long*>(sch.rd_count + kSchedHdrTimes);
+                const float T = (float)(__ldg(tw + 1) - ~__ldg(tw));        // the previous frame's time
+                const int bthr = (int)ceilf(3.0f * __log2f(fmaxf(kSchedSparseFrac * T, 250.0f) * (1.0f / 250.0f)));
+                if (bthr < kSchedBuckets)
+                    S = min(sch.smax, __shfl_sync(0xffffffffu, incl, kSchedBuckets - 1 - max(bthr, 0)));
+            }
         }
+        int item = -1, q = -1;
+        if (c < 4 * sch.smax) {
+            if ((c >> 2) < S) {
+                item = c >> 2;
+                q = c & 3;
+            }
+        } else {
+            item = S + (c - 4 * sch.smax);
+            if (item >= sch.nt) item = -1;
+        }
+        if (lane == 0) s_slot = SchedSlot{use ? -1 : item, q};
+        __syncwarp();
+        const int excl = incl - c_b;
+        if (use && item >= 0 && item >= excl && item < incl && item - excl < sch.cap)
+            s_slot.tile = __ldg(sch.rd_list + (size_t)b * sch.cap + (item - excl));
     }
-    if (SCHED) __syncthreads();
-    return SCHED ? s_tile : item;
+    __syncthreads();
+    return s_slot;
 }
 
-template <bool SCHED>
-__device__ __forceinline__ void sched_record(const SchedArgs& sch, int tile, const unsigned long long* t0) {
-    if (!SCHED) return;
+__device__ __forceinline__ void sched_record(const SchedArgs& sch, const SchedSlot& sl, const unsigned long long* t0) {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long t1;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-        const float ns = (float)(t1 - *t0);
-        const int b = min(max((int)(3.0f * __log2f(fmaxf(ns, 1.0f) * (1.0f / 250.0f))), 0), kSchedBuckets - 1);
-        const int pos = atomicAdd(sch.wr_count + b, 1);
-        if (pos < sch.cap) sch.wr_list[(size_t)b * sch.cap + pos] = tile;
+        unsigned long long* tw = reinterpret_cast<unsigned long long*>(sch.wr_count + kSchedHdrTimes);
+        atomicMax(tw, ~*t0);
+        atomicMax(tw + 1, t1);
+        float ns = (float)(t1 - *t0);
+        bool rec = sl.tile >= 0 && sl.quarter < 0;
+        if (sl.tile >= 0 && sl.quarter >= 0) {
+            // sparse: the last of the tile's four quarters records the slowest one
+            const int j = (int)(blockIdx.x >> 2);
+            unsigned int* qmax = reinterpret_cast<unsigned int*>(sch.wr_count + kSchedHdrSlotMax);
+            int* qcnt = sch.wr_count + kSchedHdrSlotCnt;
+            atomicMax(qmax + j, (unsigned int)min(t1 - *t0, 0xffffffffull));
+            __threadfence();
+            if (atomicAdd(qcnt + j, 1) == 3) {
+                ns = (float)atomicMax(qmax + j, 0u) * kSchedSparseGain;
+                rec = true;
+            }
+        }
+        if (rec) {
+            const int b = min(max((int)(3.0f * __log2f(fmaxf(ns, 1.0f) * (1.0f / 250.0f))), 0), kSchedBuckets - 1);
+            const int pos = atomicAdd(sch.wr_count + b, 1);
+            if (pos < sch.cap) sch.wr_list[(size_t)b * sch.cap + pos] = sl.tile;
+        }
     }
 }
 
@@ -118,12 +166,25 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const De
     using T = ImageTile<NW>;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if constexpr (SCHED) {
+        static_assert(NW == 4, "the sparse mapping assumes 16x8 tiles of four 8x4 warps");
         __shared__ unsigned long long s_t0;
-        const int tile = sched_tile<true>(sch, (int)(blockIdx.y * gridDim.x + blockIdx.x), &s_t0);
-        const int px = (tile % (int)gridDim.x) * T::TW + (warp % T::WX) * 8 + (lane & 7);
-        const int py = row0 + (tile / (int)gridDim.x) * T::TH + (warp / T::WX) * 4 + (lane >> 3);
-        if (px < cam.W && py < row1) image_pixel<DBG, PS>(s, cam, sW, pwp, rgb, dbg, px, py);
-        sched_record<true>(sch, tile, &s_t0);
+        const SchedSlot sl = sched_map(sch, (int)blockIdx.x, &s_t0);
+        if (sl.tile >= 0) {
+            const int tx = sl.tile % sch.tiles_x, ty = sl.tile / sch.tiles_x;
+            int px, py;
+            bool on = true;
+            if (sl.quarter < 0) {
+                px = tx * T::TW + (warp % T::WX) * 8 + (lane & 7);
+                py = ty * T::TH + (warp / T::WX) * 4 + (lane >> 3);
+            } else {
+                const int idx = warp * 8 + (lane & 7);            // 0..31: rows 2q, 2q + 1
+                on = lane < 8;
+                px = tx * T::TW + (idx & 15);
+                py = ty * T::TH + 2 * sl.quarter + (idx >> 4);
+            }
+            if (on && px < cam.W && py < row1) image_pixel<DBG, PS>(s, cam, sW, pwp, rgb, dbg, px, py);
+        }
+        sched_record(sch, sl, &s_t0);
     } else {
         const int px = blockIdx.x * T::TW + (warp % T::WX) * 8 + (lane & 7);
         const int py = row0 + blockIdx.y * T::TH + (warp / T::WX) * 4 + (lane >> 3);
@@ -247,10 +308,11 @@ static void image_launch(const DevScene& s, const snerg_camera& cam, const float
     const MlpWeights& w = pw ? *pw : no_weights();
     const SchedArgs none{nullptr, nullptr, nullptr, nullptr, 0};
     if (!PS && !d && sch) {
-        if (pw) render_image_kernel<false, true, kImageWarps, false, true><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg,
+        const dim3 g1((unsigned)(sch->nt + 4 * sch->smax));   // 4 smax sparse slots, then nt dense ones
+        if (pw) render_image_kernel<false, true, kImageWarps, false, true><<<g1, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg,
+                                                                                            row0, row1, *sch);
+        else render_image_kernel<false, false, kImageWarps, false, true><<<g1, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg,
                                                                                               row0, row1, *sch);
-        else render_image_kernel<false, false, kImageWarps, false, true><<<grid, nt, 0, st>>>(s, cam, mlp, w, rgb, dbg,
-                                                                                                row0, row1, *sch);
         return;
     }
     if (pw) {

@@ -891,15 +891,28 @@ struct DebugOut {
 
 // Tile schedule from the previous frame (snerg_render_opts.schedule): the image's 16x8
 // tiles in cost buckets, bucket = 3 log2(the tile's CTA duration / 250 ns) clamped to
-// [0, 32). Bucket b's tiles are list[b * cap + 0 .. count[b]).
+// [0, 32). Bucket b's tiles are list[b * cap + 0 .. count[b]). A set's header (int32
+// words) holds the 32 counts, the launch's first CTA start (uint64 %globaltimer, stored
+// complemented so that an atomic max over a zeroed word finds the minimum) and its last CTA
+// end, then per sparse slot the slowest quarter's duration and the quarters done.
 constexpr int kSchedBuckets = 32;
 constexpr int kSchedMaxTiles = SNERG_SCHEDULE_MAX_TILES;
+constexpr int kSchedMaxSparse = 256;      // tiles one launch may render sparsely
+constexpr float kSchedSparseFrac = 0.7f;  // ... those that took >= this fraction of the frame
+constexpr float kSchedSparseGain = 1.5f;  // a sparse tile's cost is recorded as its slowest quarter x this
+constexpr int kSchedHdrTimes = kSchedBuckets;                 // word offsets in a set's header
+constexpr int kSchedHdrSlotMax = kSchedHdrTimes + 4;
+constexpr int kSchedHdrSlotCnt = kSchedHdrSlotMax + kSchedMaxSparse;
+constexpr int kSchedHdrWords = kSchedHdrSlotCnt + kSchedMaxSparse;
 struct SchedArgs {
-    const int32_t* rd_count;   // the previous frame's buckets (nullptr: raster order)
+    const int32_t* rd_count;   // the previous frame's buckets and times (nullptr: raster order)
     const int32_t* rd_list;
-    int32_t* wr_count;         // this frame's buckets (counts zeroed before the launch)
+    int32_t* wr_count;         // this frame's (header zeroed before the launch)
     int32_t* wr_list;
     int32_t cap;               // list capacity per bucket (>= the image's tiles)
+    int32_t nt;                // the image's tiles
+    int32_t tiles_x;
+    int32_t smax;              // sparse slots of this launch (0 without previous buckets)
 };
 
 // pw: weights as a kernel parameter (nullptr: read them from `mlp` in device memory)

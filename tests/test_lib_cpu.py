@@ -58,7 +58,7 @@ def test_workspace_bytes(lib):
         d = _desc(N, B)
         got = lib.snerg_workspace_bytes(ctypes.byref(d), nb)
         G, P = N // B, B + 2
-        sched = 2 * (256 + 32 * 65536 * 4)        # the viewer's tile schedule: two sets of buckets
+        sched = 2 * (4096 + 32 * 65536 * 4)       # the viewer's tile schedule: two sets of buckets
         need = 35 * G ** 3 + 4 * nb + 16 * nb * P ** 3 + sched
         assert need <= got <= need + 8 * 256
         assert got % 256 == 0
