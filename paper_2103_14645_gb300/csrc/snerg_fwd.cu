@@ -31,9 +31,8 @@ struct ImageTile {
 // whatever the order and mapping. Each CTA records its duration when all its warps are
 // done (a sparse tile by its last quarter to finish, as its slowest quarter times
 // kSchedSparseGain: about its dense cost, so that it stays sparse while it stays slow) and
-// the launch's start and end. The grid is
-// nt + 4 smax CTAs: 4 smax sparse slots (S <= smax used), then nt dense slots for the tiles
-// S .. nt - 1 of the order (the last S of them idle).
+// the launch's start and end. The grid is nt + 4 smax CTAs: 4 smax sparse slots (S <= smax
+// used), then nt dense slots for the tiles S .. nt - 1 of the order (the last S idle).
 struct SchedSlot {
     int tile;       // -1: idle
     int quarter;    // -1: dense
