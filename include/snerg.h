@@ -388,6 +388,12 @@ snerg_status snerg_last_status(snerg_handle h, void* stream);
 /* Number of kernels the library launched through this handle since creation. */
 int64_t snerg_launch_count(snerg_handle h);
 
+/* SYNCHRONISES `stream`. What the handle's last snerg_render with schedule = 1 did:
+ * *ordered = 1 if it launched its tiles in the order recorded on the render before (0:
+ * raster order), *sparse_tiles = how many of its slowest tiles it rendered sparsely (0 and 0
+ * if there was no such render). For tests and tuning; the render does not need it. */
+snerg_status snerg_schedule_stats(snerg_handle h, void* stream, int32_t* sparse_tiles, int32_t* ordered);
+
 /* Tile shape and CTAs/SM chosen by the last persistent launch (or 0s). */
 snerg_status snerg_persistent_config(snerg_handle h, int32_t* tile_w, int32_t* tile_h,
                                      int32_t* ctas_per_sm);

@@ -674,6 +674,25 @@ extern "C" snerg_status snerg_set_mlp(snerg_handle h, const float* mlp) {
 
 extern "C" int64_t snerg_launch_count(snerg_handle h) { return h ? h->launches : 0; }
 
+extern "C" snerg_status snerg_schedule_stats(snerg_handle h, void* stream, int32_t* sparse_tiles, int32_t* ordered) {
+    if (!h || !sparse_tiles || !ordered) return SNERG_E_INVAL;
+    *sparse_tiles = 0;
+    *ordered = 0;
+    if (!h->sched_valid) return SNERG_OK;
+    Layout L;
+    make_layout(&h->desc, h->nb, &L);
+    // the set the last scheduled launch wrote is the one the next launch will read
+    const int32_t* hdr = (const int32_t*)(h->ws + L.sched + (size_t)h->sched_set * kSchedSetBytes);
+    int32_t info[2] = {0, 0};
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(info, hdr + kSchedHdrInfo, sizeof(info), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return SNERG_E_CUDA;
+    *sparse_tiles = info[0] > 0 ? info[0] - 1 : 0;
+    *ordered = info[1];
+    return SNERG_OK;
+}
+
 extern "C" snerg_status snerg_persistent_config(snerg_handle h, int32_t* tile_w, int32_t* tile_h,
                                                 int32_t* ctas_per_sm) {
     if (!h || !tile_w || !tile_h || !ctas_per_sm) return SNERG_E_INVAL;

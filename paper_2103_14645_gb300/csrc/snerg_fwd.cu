@@ -78,7 +78,13 @@ __device__ __forceinline__ SchedSlot sched_map(const SchedArgs& sch, int c, unsi
             item = S + (c - 4 * sch.smax);
             if (item >= sch.nt) item = -1;
         }
-        if (lane == 0) s_slot = SchedSlot{use ? -1 : item, q};
+        if (lane == 0) {
+            s_slot = SchedSlot{use ? -1 : item, q};
+            if (c == 0) {           // what this launch did, for snerg_schedule_stats
+                sch.wr_count[kSchedHdrInfo] = S + 1;
+                sch.wr_count[kSchedHdrInfo + 1] = use ? 1 : 0;
+            }
+        }
         __syncwarp();
         const int excl = incl - c_b;
         if (use && item >= 0 && item >= excl && item < incl && item - excl < sch.cap)

@@ -903,7 +903,9 @@ constexpr float kSchedSparseGain = 1.5f;  // a sparse tile's cost is recorded as
 constexpr int kSchedHdrTimes = kSchedBuckets;                 // word offsets in a set's header
 constexpr int kSchedHdrSlotMax = kSchedHdrTimes + 4;
 constexpr int kSchedHdrSlotCnt = kSchedHdrSlotMax + kSchedMaxSparse;
-constexpr int kSchedHdrWords = kSchedHdrSlotCnt + kSchedMaxSparse;
+constexpr int kSchedHdrInfo = kSchedHdrSlotCnt + kSchedMaxSparse;   // tiles rendered sparsely + 1, and
+                                                                    // 1 if the previous order was used
+constexpr int kSchedHdrWords = kSchedHdrInfo + 2;
 struct SchedArgs {
     const int32_t* rd_count;   // the previous frame's buckets and times (nullptr: raster order)
     const int32_t* rd_list;

@@ -32,7 +32,7 @@ EXPORTED = ["snerg_workspace_bytes", "snerg_create", "snerg_render", "snerg_rend
             "snerg_persistent_config", "snerg_destroy", "snerg_status_str", "snerg_render_rays_noalloc",
             "snerg_set_mlp", "snerg_l2_loss", "snerg_adam_step", "snerg_bake_workspace_bytes", "snerg_bake",
             "snerg_requantize_atlas", "snerg_grad_blocks_touched", "snerg_grad_blocks_gather",
-            "snerg_grad_blocks_scatter", "snerg_render_to_host", "snerg_train_rays"]
+            "snerg_grad_blocks_scatter", "snerg_render_to_host", "snerg_train_rays", "snerg_schedule_stats"]
 MAX_BAKE_BLOBS = 64
 
 
@@ -105,6 +105,8 @@ def load_library(path: str = LIB_PATH):
     lib.snerg_render_rays_noalloc.restype = ctypes.c_int
     lib.snerg_train_rays.argtypes = [P, P, i32, P, i64, P, P, P, P, P, P, P]
     lib.snerg_train_rays.restype = ctypes.c_int
+    lib.snerg_schedule_stats.argtypes = [P, P, P, P]
+    lib.snerg_schedule_stats.restype = ctypes.c_int
     lib.snerg_render_to_host.argtypes = [P, P, i32, P, P, P, i32, P]
     lib.snerg_render_to_host.restype = ctypes.c_int
     lib.snerg_grad_blocks_touched.argtypes = [P, i64, i32, P, P]
@@ -197,6 +199,14 @@ class Renderer:
     @property
     def launches(self) -> int:
         return int(self.lib.snerg_launch_count(self.handle))
+
+    def schedule_stats(self):
+        """(tiles rendered sparsely, 1 if the previous order was used) of the last render
+        with schedule=True (snerg_schedule_stats; synchronises)."""
+        sp, od = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.snerg_schedule_stats(self.handle, _stream(self.device), ctypes.byref(sp), ctypes.byref(od)),
+               "snerg_schedule_stats")
+        return sp.value, od.value
 
     def persistent_config(self):
         tw, th, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

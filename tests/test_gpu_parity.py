@@ -475,12 +475,24 @@ def test_tile_schedule_reproduces_raster_renders():
         other = np.asarray([synth.look_at_camera(synth.CAM_RADIUS * np.array([0.0, 1.0, 0.2]), (0.0, 0.0, 0.0),
                                                  61, 37, 39.0)])
         seq = cams[:2] + [other] + cams[2:] + [other]
+        assert r.schedule_stats() == (0, 0)
+        sparse = []
+        prev = None
         for k, cam in enumerate(seq):
             mlp = w if k % 2 else None
             want = r.render(cam, mlp).cpu().numpy()
             got = r.render(cam, mlp, schedule=True).cpu().numpy()
             np.testing.assert_array_equal(got, want)
+            sp, ordered = r.schedule_stats()
+            # a frame follows the recorded order when the scheduled frame before had its size
+            size = (int(cam[0]["W"]), int(cam[0]["H"]))
+            assert ordered == (1 if size == prev else 0), (k, ordered)
+            assert sp == 0 or ordered == 1
+            sparse.append(sp)
+            prev = size
         r.check_status()
+        if name == "shell1024":
+            assert max(sparse) > 0      # the slowest tiles of the 800x800 view were rendered sparsely
 
 
 def test_parameter_weights_match_device_weights():
