@@ -504,10 +504,10 @@ def training_rooflines(cnt, n, ms_fb, ms_tr, tag):
     adj = ADJ_BYTES_PER_SAMPLE * cnt[1] + MLP_GRAD_BYTES_PER_CTA * ctas
     two = (march_bytes(cnt, n) + 12 * n + 48 * n) + (72 * n + adj)
     one = march_bytes(cnt, n) + 24 * n + adj
-    return (roofline(two, ms_fb, "render_rays_kernel + backward_rays_kernel",
+    return (roofline(two, ms_fb, "render_rays_kernel + backward_rays_kernel<0, 1>",
                      profile=[(f"render_rays_{tag}", FWD_SOURCES), (f"backward_rays_{tag}", BWD_SOURCES)],
                      launches=2),
-            roofline(one, ms_tr, "backward_rays_kernel<1> (snerg_train_rays)", profile=f"train_rays_{tag}",
+            roofline(one, ms_tr, "backward_rays_kernel<1, 0> (snerg_train_rays)", profile=f"train_rays_{tag}",
                      sources=BWD_SOURCES))
 
 

@@ -2,12 +2,13 @@
 // fine-tuned against an L2 image loss, Eq. 3; the gradient here also reaches the baked
 // colour and feature values, with density frozen).
 //
-// One thread per ray. Nothing of the forward march is stored: the kernel re-marches
-// the ray to get C_d, V, T and the MLP input, runs the MLP adjoint in registers, then
-// marches the ray a second time and scatters w_k * (trilinear weight) * dL/d(C_d, V)
-// into the FP32 gradient atlas with vector atomics. Because density is frozen the
-// composite weights w_k depend only on the samples before k, so the second pass walks
-// the ray in forward order and needs no per-sample state. MLP weight gradients are
+// One thread per ray. The kernel marches the ray to get C_d, V, T and the MLP input
+// (recording the lattice indices of its first kRecCap composited samples), runs the MLP
+// adjoint in registers, then scatters w_k * (trilinear weight) * dL/d(C_d, V) into the
+// FP32 gradient atlas with vector atomics. Because density is frozen the composite
+// weights w_k depend only on the samples before k, so the scatter walks the recorded
+// samples in forward order, recomputing their weights, and marches on from the last
+// of them only for a ray that composited more. MLP weight gradients are
 // summed over the CTA's rays from activations staged in shared memory and reach global
 // memory with one atomic per parameter per CTA.
 #include <atomic>
@@ -175,14 +176,15 @@ __device__ __forceinline__ void dphi_sums(const float* rows, float* grad_mlp) {
     }
 }
 
-// fwd_aux / fwd_counts (nullable, both or neither): the forward's per-ray outputs
-// (C_d, V, opacity; steps, composited samples, indirection reads, first composited
-// lattice index). With them the kernel skips its own first march.
+// STATE: fwd_aux / fwd_counts hold the forward's per-ray outputs (C_d, V, opacity;
+// steps, composited samples, indirection reads, first composited lattice index); the
+// kernel then skips its own first march and scatters with one march from the first
+// composited sample.
 // TRAIN: one fine-tuning step for the ray in one pass (Sec. 5.5, Eq. 3): the march and the
 // MLP give C, the L2 loss |C - C*|^2 is accumulated into *loss, dL/dC = 2 (C - C*) is taken
 // in the kernel, and the adjoint follows as for a given upstream gradient; C goes to
 // rgb_out (nullable). grad_rgb, fwd_aux and fwd_counts are not used.
-template <bool TRAIN>
+template <bool TRAIN, bool STATE>
 __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     const DevScene s, const __grid_constant__ CamTable cams, int32_t n_cams, const int32_t* __restrict__ pix,
     int64_t n, const float* __restrict__ mlp, const float* __restrict__ grad_rgb,
@@ -205,20 +207,22 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     st.active = 0;
     st.T = 1.0f;
     int k_first = 0;
+    int krec[kRecCap];             // the first march's composited lattice indices
     if (i < n) {
         const int ci = __ldg(pix + 3 * i), px = __ldg(pix + 3 * i + 1), py = __ldg(pix + 3 * i + 2);
         if (ci >= 0 && ci < n_cams && px >= 0 && py >= 0 && px < cams.c[ci].W && py < cams.c[ci].H)
             r = make_ray(s, cams.c[ci], px, py);
         else
             atomicCAS(s.status, 0, (int)SNERG_E_INVAL);
-        if (!TRAIN && fwd_aux) {
+        if (STATE) {
             // the forward's per-ray state: C_d, V (decoded) and the first composited index
             st.active = r.hit ? __ldg(fwd_counts + 4 * i + 1) : 0;
             k_first = __ldg(fwd_counts + 4 * i + 3);
 #pragma unroll
             for (int c = 0; c < 7; ++c) st.acc[c] = __ldg(fwd_aux + kAuxCh * i + c) * 255.0f;
         } else {
-            march<false, false, false, true>(s, r, st, nullptr, 0, nullptr, nullptr, 0, &k_first);
+            march<false, false, false, true, true>(s, r, st, nullptr, 0, nullptr, nullptr, 0, &k_first, nullptr,
+                                                   nullptr, krec);
             record_status(s, st);
         }
     }
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
         const float inv255 = 1.0f / 255.0f;
         float cd[3], v[4];
         float T;
-        if (!TRAIN && fwd_aux) {
+        if (STATE) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) cd[c] = __ldg(fwd_aux + kAuxCh * i + c);
 #pragma unroll
@@ -303,10 +307,19 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
         for (int c = 0; c < 3; ++c) gf[c] = sc * (g[c] + gx[c]);     // C = s C_d + residual
 #pragma unroll
         for (int c = 0; c < 4; ++c) gf[3 + c] = sc * gx[3 + c];
-        // the second pass starts at the first composited sample: nothing before it
-        // contributes (T = 1 and tau = 0 there), so its weights are the first pass's
         MarchState st2;
-        march<false, true, false, true>(s, r, st2, nullptr, 0, gf, grad_atlas, k_first);
+        if (!STATE) {
+            scatter_recorded(s, r, krec, min(st.active, kRecCap), gf, grad_atlas, st2);
+            // a ray with more composited samples marches on from the last recorded one
+            if (st.active > kRecCap)
+                march<false, true, false, true, false, true>(s, r, st2, nullptr, 0, gf, grad_atlas,
+                                                             krec[kRecCap - 1] + 1);
+        } else {
+            // without a recording (the forward's per-ray state given) a second march starts
+            // at the first composited sample: nothing before it contributes (T = 1 and
+            // tau = 0 there), so its weights are the first pass's
+            march<false, true, false, true>(s, r, st2, nullptr, 0, gf, grad_atlas, k_first);
+        }
     }
     if (TRAIN && loss) {
         float v = l2;
@@ -325,7 +338,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     if (grad_mlp) dphi_sums(rows, grad_mlp);
 }
 
-template <bool TRAIN>
+template <bool TRAIN, bool STATE>
 static cudaError_t backward_launch(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
                                    int64_t n, const float* mlp, const float* grad_rgb, const float* fwd_aux,
                                    const int32_t* fwd_counts, const float* target, float* rgb_out, float* loss,
@@ -339,28 +352,32 @@ static cudaError_t backward_launch(const DevScene& s, const CamTable& cams, int3
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     if (!attr_set[dev].load()) {
-        e = cudaFuncSetAttribute(backward_rays_kernel<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(backward_rays_kernel<TRAIN, STATE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return e;
         attr_set[dev].store(true);
     }
     const unsigned grid = (unsigned)((n + kBwdThreads - 1) / kBwdThreads);
-    backward_rays_kernel<TRAIN><<<grid, kBwdThreads, smem, st>>>(s, cams, n_cams, pix, n, mlp, grad_rgb, fwd_aux,
-                                                                 fwd_counts, target, rgb_out, loss, grad_atlas,
-                                                                 grad_mlp);
+    backward_rays_kernel<TRAIN, STATE><<<grid, kBwdThreads, smem, st>>>(s, cams, n_cams, pix, n, mlp, grad_rgb,
+                                                                        fwd_aux, fwd_counts, target, rgb_out, loss,
+                                                                        grad_atlas, grad_mlp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
                                  int64_t n, const float* mlp, const float* grad_rgb, const float* fwd_aux,
                                  const int32_t* fwd_counts, float* grad_atlas, float* grad_mlp, cudaStream_t st) {
-    return backward_launch<false>(s, cams, n_cams, pix, n, mlp, grad_rgb, fwd_aux, fwd_counts, nullptr, nullptr,
-                                  nullptr, grad_atlas, grad_mlp, st);
+    if (fwd_aux)
+        return backward_launch<false, true>(s, cams, n_cams, pix, n, mlp, grad_rgb, fwd_aux, fwd_counts, nullptr,
+                                            nullptr, nullptr, grad_atlas, grad_mlp, st);
+    return backward_launch<false, false>(s, cams, n_cams, pix, n, mlp, grad_rgb, nullptr, nullptr, nullptr, nullptr,
+                                         nullptr, grad_atlas, grad_mlp, st);
 }
 
 cudaError_t launch_train_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
                               const float* mlp, const float* target, float* rgb_out, float* loss, float* grad_atlas,
                               float* grad_mlp, cudaStream_t st) {
-    return backward_launch<true>(s, cams, n_cams, pix, n, mlp, nullptr, nullptr, nullptr, target, rgb_out, loss,
+    return backward_launch<true, false>(s, cams, n_cams, pix, n, mlp, nullptr, nullptr, nullptr, target, rgb_out, loss,
                                  grad_atlas, grad_mlp, st);
 }
 

@@ -345,9 +345,88 @@ __device__ __forceinline__ void load_stencil(const float u[3], const float o[3],
     cv[7] = __ldg(p0 + PP + P + 1);
 }
 
+// Density trilinear of one composited sample (binary32, x then y then z) and its
+// compositing (Eqs. 2, 5, 6): returns w_k and advances T (and tau); saturated once the
+// ray's remaining transmittance is below the early-exit bound.
+__device__ __forceinline__ float composite(const DevScene& s, const uint2 cv[8], const float f[3], const float g[3],
+                                           float& T, float& tau, bool& saturated) {
+    const float e00 = __fadd_rn(__fmul_rn(code(cv[0].x, 0), g[0]), __fmul_rn(code(cv[1].x, 0), f[0]));
+    const float e10 = __fadd_rn(__fmul_rn(code(cv[2].x, 0), g[0]), __fmul_rn(code(cv[3].x, 0), f[0]));
+    const float e01 = __fadd_rn(__fmul_rn(code(cv[4].x, 0), g[0]), __fmul_rn(code(cv[5].x, 0), f[0]));
+    const float e11 = __fadd_rn(__fmul_rn(code(cv[6].x, 0), g[0]), __fmul_rn(code(cv[7].x, 0), f[0]));
+    const float e0 = __fadd_rn(__fmul_rn(e00, g[1]), __fmul_rn(e10, f[1]));
+    const float e1 = __fadd_rn(__fmul_rn(e01, g[1]), __fmul_rn(e11, f[1]));
+    const float sq = __fadd_rn(__fmul_rn(e0, g[2]), __fmul_rn(e1, f[2]));
+    float wk;
+    if (s.flags & SNERG_FLAG_ALPHA_ATLAS) {
+        // channel 0 holds alpha: a = s * binary32(1/255), T <- T (1 - a) in binary32,
+        // stop once T < binary32(1e-3)
+        const float a = __fmul_rn(sq, s.inv255);
+        wk = T * a;
+        T = __fmul_rn(T, __fsub_rn(1.0f, a));
+        saturated = T < s.tmin;
+    } else {
+        const float od = __fmul_rn(sq, s.kappa);
+        tau = __fadd_rn(tau, od);
+        const float e = expf(-od);
+        wk = T * (1.0f - e);
+        T *= e;
+        saturated = tau > s.taumax;
+    }
+    return wk;
+}
+
+// The adjoint of one composited sample's colour/feature fetch: w_k * (corner weight) *
+// gfeat into the eight corners' gradient entries ([slot][B^3][8], channel 0 unused) with
+// vector atomics. o: the sample's block origin minus one, fl its stencil's lower corner.
+__device__ __forceinline__ void scatter_sample(const DevScene& s, int slot, const float fl[3], const float o[3],
+                                               const float f[3], const float g[3], float wk, const float* gfeat,
+                                               float* grad_atlas) {
+    const int B = s.B, N = s.N;
+    float tw[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) tw[c] = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
+    const int B3 = B * B * B;
+    // a stencil inside this block (lower corner at padded coordinate 1 .. B-1 on every
+    // axis) has all eight corners in its own slot: no indirection reads
+    const float ex = fl[0] - o[0], ey = fl[1] - o[1], ez = fl[2] - o[2];
+    const float Bm = (float)(B - 1);
+    if (ex >= 1.0f && ex <= Bm && ey >= 1.0f && ey <= Bm && ez >= 1.0f && ez <= Bm) {
+        float* g0 = grad_atlas + ((size_t)slot * B3 + (((int)ez - 1) * B + ((int)ey - 1)) * B + ((int)ex - 1)) * 8;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float* gp = g0 + ((((c >> 2) & 1) * B + ((c >> 1) & 1)) * B + (c & 1)) * 8;
+            const float w = wk * tw[c];
+            atomicAdd(reinterpret_cast<float4*>(gp), make_float4(0.0f, w * gfeat[0], w * gfeat[1], w * gfeat[2]));
+            atomicAdd(reinterpret_cast<float4*>(gp + 4),
+                      make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int X = min(max((int)fl[0] + (c & 1), 0), N - 1);
+            const int Y = min(max((int)fl[1] + ((c >> 1) & 1), 0), N - 1);
+            const int Z = min(max((int)fl[2] + ((c >> 2) & 1), 0), N - 1);
+            const int cs = __ldg(s.ind + (((Z >> s.lgB) * s.G + (Y >> s.lgB)) * s.G + (X >> s.lgB)));
+            if (cs < 0) continue;
+            const int loc = (((Z & (B - 1)) * B) + (Y & (B - 1))) * B + (X & (B - 1));
+            float* gp = grad_atlas + ((size_t)cs * B3 + loc) * 8;
+            const float w = wk * tw[c];
+            atomicAdd(reinterpret_cast<float4*>(gp), make_float4(0.0f, w * gfeat[0], w * gfeat[1], w * gfeat[2]));
+            atomicAdd(reinterpret_cast<float4*>(gp + 4),
+                      make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
+        }
+    }
+}
+
+// Composited samples a march records (REC) for the adjoint's scatter
+constexpr int kRecCap = 32;
+
 // ---------------------------------------------------------------------------------
 // the march. TRACE records visited voxels; GRAD scatters w_k * trilinear weight * g
-// into the gradient atlas (density frozen, so the weights are the forward ones).
+// into the gradient atlas (density frozen, so the weights are the forward ones); REC
+// stores the lattice indices of the first kRecCap composited samples in krec; CONT
+// starts from the T and tau already in st (a march resumed after recorded samples).
 // ---------------------------------------------------------------------------------
 // k_begin: first lattice index to consider (0, or a k known to precede every composited
 // sample, in which case the result is the same); k_first (nullable) receives the index
@@ -359,17 +438,20 @@ __device__ __forceinline__ void per_sample_residual(const MlpWeights* pw, const 
 // PS: the non-deferred comparison model (SNERG_FLAG_PER_SAMPLE_MLP): every composited
 // sample also evaluates the view-dependence MLP on its own (c_d, v) (weights from pw, else
 // from sW) and adds w_k (c_d,k + residual_k) to st.rgb_ps.
-template <bool TRACE, bool GRAD, bool PS = false, bool SPEC = false>
+template <bool TRACE, bool GRAD, bool PS = false, bool SPEC = false, bool REC = false, bool CONT = false>
 __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchState& st,
                                       uint64_t* trace, int trace_cap,
                                       const float* gfeat, float* grad_atlas,
                                       int k_begin = 0, int* k_first = nullptr,
-                                      const MlpWeights* ps_w = nullptr, const float* ps_sw = nullptr) {
+                                      const MlpWeights* ps_w = nullptr, const float* ps_sw = nullptr,
+                                      int* krec = nullptr) {
 #pragma unroll
     for (int c = 0; c < 7; ++c) st.acc[c] = 0.0f;
     st.rgb_ps[0] = st.rgb_ps[1] = st.rgb_ps[2] = 0.0f;
-    st.T = 1.0f;
-    st.tau = 0.0f;
+    if (!CONT) {
+        st.T = 1.0f;
+        st.tau = 0.0f;
+    }
     st.steps = 0;
     st.active = 0;
     st.blocks = 0;
@@ -464,35 +546,12 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 trace[st.active] = ((uint64_t)nearest_voxel(u[2], N) * N + (uint64_t)nearest_voxel(u[1], N)) * N +
                                    (uint64_t)nearest_voxel(u[0], N);
             if (k_first && st.active == 0) *k_first = (int)kk;
+            if (REC && st.active < kRecCap) krec[st.active] = (int)kk;
             st.active++;
             // trilinear stencil on the virtual grid, cell-centred
             if (!spec) load_stencil(u, o3, P, s.P3, pa, f, g, fl, cv);
-            // binary32 control: density trilinear, x then y then z
-            const float e00 = __fadd_rn(__fmul_rn(code(cv[0].x, 0), g[0]), __fmul_rn(code(cv[1].x, 0), f[0]));
-            const float e10 = __fadd_rn(__fmul_rn(code(cv[2].x, 0), g[0]), __fmul_rn(code(cv[3].x, 0), f[0]));
-            const float e01 = __fadd_rn(__fmul_rn(code(cv[4].x, 0), g[0]), __fmul_rn(code(cv[5].x, 0), f[0]));
-            const float e11 = __fadd_rn(__fmul_rn(code(cv[6].x, 0), g[0]), __fmul_rn(code(cv[7].x, 0), f[0]));
-            const float e0 = __fadd_rn(__fmul_rn(e00, g[1]), __fmul_rn(e10, f[1]));
-            const float e1 = __fadd_rn(__fmul_rn(e01, g[1]), __fmul_rn(e11, f[1]));
-            const float sq = __fadd_rn(__fmul_rn(e0, g[2]), __fmul_rn(e1, f[2]));
-            // compositing (Eqs. 2, 5, 6)
-            float wk;
             bool saturated;
-            if (s.flags & SNERG_FLAG_ALPHA_ATLAS) {
-                // channel 0 holds alpha: a = s * binary32(1/255), T <- T (1 - a) in binary32,
-                // stop once T < binary32(1e-3)
-                const float a = __fmul_rn(sq, s.inv255);
-                wk = st.T * a;
-                st.T = __fmul_rn(st.T, __fsub_rn(1.0f, a));
-                saturated = st.T < s.tmin;
-            } else {
-                const float od = __fmul_rn(sq, s.kappa);
-                st.tau = __fadd_rn(st.tau, od);
-                const float e = expf(-od);
-                wk = st.T * (1.0f - e);
-                st.T *= e;
-                saturated = st.tau > s.taumax;
-            }
+            const float wk = composite(s, cv, f, g, st.T, st.tau, saturated);
             accumulate_colour(st, cv, wk, f, g);
             if (PS) {
                 // this sample's own decoded colour and features, then its residual
@@ -516,46 +575,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
 #pragma unroll
                 for (int c = 0; c < 3; ++c) st.rgb_ps[c] = fmaf(wk, cdk[c] + res[c], st.rgb_ps[c]);
             }
-            if (GRAD) {
-                float tw[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    tw[c] = ((c & 4) ? f[2] : g[2]) * ((c & 2) ? f[1] : g[1]) * ((c & 1) ? f[0] : g[0]);
-                const int B3 = B * B * B;
-                // a stencil inside this block (lower corner at padded coordinate 1 .. B-1 on
-                // every axis) has all eight corners in its own slot: no indirection reads
-                const float ex = fl[0] - ox, ey = fl[1] - oy, ez = fl[2] - oz;
-                const float Bm = (float)(B - 1);
-                if (ex >= 1.0f && ex <= Bm && ey >= 1.0f && ey <= Bm && ez >= 1.0f && ez <= Bm) {
-                    float* g0 = grad_atlas +
-                                ((size_t)slot * B3 + (((int)ez - 1) * B + ((int)ey - 1)) * B + ((int)ex - 1)) * 8;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        float* gp = g0 + ((((c >> 2) & 1) * B + ((c >> 1) & 1)) * B + (c & 1)) * 8;
-                        const float w = wk * tw[c];
-                        atomicAdd(reinterpret_cast<float4*>(gp),
-                                  make_float4(0.0f, w * gfeat[0], w * gfeat[1], w * gfeat[2]));
-                        atomicAdd(reinterpret_cast<float4*>(gp + 4),
-                                  make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
-                    }
-                } else {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int X = min(max((int)fl[0] + (c & 1), 0), N - 1);
-                    const int Y = min(max((int)fl[1] + ((c >> 1) & 1), 0), N - 1);
-                    const int Z = min(max((int)fl[2] + ((c >> 2) & 1), 0), N - 1);
-                    const int cs = __ldg(s.ind + (((Z >> s.lgB) * s.G + (Y >> s.lgB)) * s.G + (X >> s.lgB)));
-                    if (cs < 0) continue;
-                    const int loc = (((Z & (B - 1)) * B) + (Y & (B - 1))) * B + (X & (B - 1));
-                    float* gp = grad_atlas + ((size_t)cs * B3 + loc) * 8;
-                    const float w = wk * tw[c];
-                    atomicAdd(reinterpret_cast<float4*>(gp),
-                              make_float4(0.0f, w * gfeat[0], w * gfeat[1], w * gfeat[2]));
-                    atomicAdd(reinterpret_cast<float4*>(gp + 4),
-                              make_float4(w * gfeat[3], w * gfeat[4], w * gfeat[5], w * gfeat[6]));
-                }
-                }
-            }
+            if (GRAD) scatter_sample(s, slot, fl, o3, f, g, wk, gfeat, grad_atlas);
             if (saturated) {
                 steps += kk - k + 1.0f;
                 done = true;
@@ -569,6 +589,45 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
         k = kx;
     }
     st.steps = (int)steps;
+}
+
+// The adjoint scatter (march<..., GRAD>'s) of the n composited samples a march recorded
+// (REC), without the block entries and probes between them: each sample's block, stencil
+// and weight are recomputed exactly as the march computed them (the same lattice index,
+// the same binary32 control arithmetic, T and tau carried in the same order), so the
+// scattered values are those of a second march. T and tau after the last sample are left
+// in st for a march that continues from the next lattice index (CONT).
+__device__ __forceinline__ void scatter_recorded(const DevScene& s, const Ray& r, const int* krec, int n,
+                                                 const float* gfeat, float* grad_atlas, MarchState& st) {
+    st.T = 1.0f;
+    st.tau = 0.0f;
+    const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
+    const int32_t* ind = s.ind + oct * s.ind_oct;
+    int bprev = -1, slot = -1;
+    for (int j = 0; j < n; ++j) {
+        const float t = lattice_t(r, (float)krec[j]);
+        float u[3];
+        int b[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            u[i] = lattice_u(r, t, i);
+            b[i] = nearest_voxel(u[i], s.N) >> s.lgB;
+        }
+        const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
+        if (bi != bprev) {
+            slot = __ldg(ind + bi);
+            bprev = bi;
+        }
+        if (slot < 0) continue;     // not a block with samples: never recorded by a march
+        const float o3[3] = {(float)((b[0] << s.lgB) - 1), (float)((b[1] << s.lgB) - 1),
+                             (float)((b[2] << s.lgB) - 1)};
+        float f[3], g[3], fl[3];
+        uint2 cv[8];
+        load_stencil(u, o3, s.P, s.P3, s.patlas + (size_t)slot * s.P3, f, g, fl, cv);
+        bool saturated;
+        const float wk = composite(s, cv, f, g, st.T, st.tau, saturated);
+        scatter_sample(s, slot, fl, o3, f, g, wk, gfeat, grad_atlas);
+    }
 }
 
 // ---------------------------------------------------------------------------------

@@ -286,6 +286,48 @@ def test_backward_matches_oracle_gradient(name, n):
     assert np.abs(gm - rm).max() <= 1e-4 * sm
 
 
+@pytest.mark.parametrize("sigma_vox,flags", [(0.05, 0), (0.3, 0), (0.3, renderer.FLAG_ALPHA_ATLAS)])
+def test_backward_rays_longer_than_the_recording(sigma_vox, flags):
+    """The adjoint's first march records its first 32 composited samples; the scatter
+    walks those and marches on from the last of them. Here most rays composite more (up to
+    ~100 samples of a thin medium): the backward and the fused training step against the
+    FP64 oracle, and both against the backward that takes the forward's per-ray state
+    (one march from the first composited sample)."""
+    sc0 = _gauss_scene(128, 16, 0.5, sigma_vox, 3, [(40, 33), (17, 29), (30, 30)])
+    atl = sc0.atlas.copy()
+    if flags & renderer.FLAG_ALPHA_ATLAS:
+        atl[..., 0] = (atl[..., 0] + 7) // 8          # a thin medium of alpha codes
+    sc = synth.custom_scene(sc0.N, sc0.B, sc0.ind, atl, sc0.sigma_max, sc0.mlp, sc0.cameras, flags=flags)
+    pix_np, g_np = _bwd_case(sc, 2048, 9)
+    o = oracle.render_rays(sc, pix_np)
+    assert (o["counts"][:, 1] > 32).sum() > 500 and (o["counts"][:, 1] > 64).any()
+    ga, gm, r = gpu_backward(sc, pix_np, g_np)
+    ra, rm = oracle.backward_rays(sc, pix_np, g_np)
+    assert np.abs(ga - ra).max() <= 1e-4 * np.abs(ra).max()
+    assert np.abs(gm - rm).max() <= 1e-4 * np.abs(rm).max()
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    pix = torch.from_numpy(pix_np).to(DEV)
+    fwd = r.render_rays(sc.cameras, pix, w, aux=True, counts=True)
+    ga2 = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=DEV)
+    gm2 = torch.zeros(883, dtype=torch.float32, device=DEV)
+    r.backward(sc.cameras, pix, w, torch.from_numpy(g_np).to(DEV), ga2, gm2, fwd_aux=fwd["aux"],
+               fwd_counts=fwd["counts"])
+    r.check_status()
+    np.testing.assert_allclose(ga, ga2.cpu().numpy(), rtol=0, atol=1e-6 * np.abs(ga).max())
+    # the fused step for dL/dC = 2 (C - C*): its gradients against the backward's for that dL/dC
+    target = np.random.default_rng(10).uniform(size=(pix_np.shape[0], 3)).astype(np.float32)
+    ga3 = torch.zeros_like(ga2)
+    gm3 = torch.zeros_like(gm2)
+    rgb = torch.empty((pix_np.shape[0], 3), dtype=torch.float32, device=DEV)
+    r.train_rays(sc.cameras, pix, w, torch.from_numpy(target).to(DEV), ga3, gm3, out=rgb)
+    r.check_status()
+    gd = 2.0 * (rgb - torch.from_numpy(target).to(DEV))
+    ga4, _, _ = gpu_backward(sc, pix_np, gd.cpu().numpy())
+    np.testing.assert_allclose(ga3.cpu().numpy(), ga4, rtol=0, atol=1e-5 * np.abs(ga4).max())
+    ra3, _ = oracle.backward_rays(sc, pix_np, 2.0 * (o["rgb"] - target))
+    assert np.abs(ga3.cpu().numpy() - ra3).max() <= 1e-4 * np.abs(ra3).max()
+
+
 def test_backward_mlp_central_differences():
     """GPU gradient w.r.t. 64 sampled MLP weights vs central differences (h = 1e-3) of
     the GPU forward, L = 1/2 sum |C - target|^2 over 4096 rays of the 512^3 scene."""
