@@ -27,6 +27,64 @@ constexpr int kMaxDevices = 64;     // transposed weights (883) rounded up to a 
 
 size_t backward_smem_bytes() { return (size_t)(kWFloats + kBwdThreads * kRow) * sizeof(float); }
 
+// One recorded sample's block slot, stencil and trilinear weights (march order: the
+// block of the sample's nearest voxel, its padded-atlas stencil).
+struct RecSample {
+    float o3[3], f[3], g[3], fl[3];
+    uint2 cv[8];
+    int slot;
+};
+
+__device__ __forceinline__ void fetch_recorded(const DevScene& s, const Ray& r, const int32_t* ind, int k,
+                                               int& bprev, int& slot, RecSample& x) {
+    const float t = lattice_t(r, (float)k);
+    float u[3];
+    int b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        u[i] = lattice_u(r, t, i);
+        b[i] = nearest_voxel(u[i], s.N) >> s.lgB;
+    }
+    const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
+    if (bi != bprev) {
+        slot = __ldg(ind + bi);
+        bprev = bi;
+    }
+    x.slot = slot;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x.o3[i] = (float)((b[i] << s.lgB) - 1);
+    // a block without samples is never recorded by a march; its slot only guards the address
+    load_stencil(u, x.o3, s.P, s.P3, s.patlas + (size_t)max(slot, 0) * s.P3, x.f, x.g, x.fl, x.cv);
+}
+
+// The adjoint scatter (march<..., GRAD>'s) of the n composited samples a march recorded
+// (REC), without the block entries and probes between them: each sample's block, stencil
+// and weight are recomputed exactly as the march computed them (the same lattice index,
+// the same binary32 control arithmetic, T and tau carried in the same order), so the
+// scattered values are those of a second march. The next sample's stencil is fetched
+// before the current one is composited, so that its latency overlaps. T and tau after the
+// last sample are left in st for a march that continues from the next lattice index (CONT).
+__device__ __forceinline__ void scatter_recorded(const DevScene& s, const Ray& r, const int* krec, int n,
+                                                 const float* gfeat, float* grad_atlas, MarchState& st) {
+    st.T = 1.0f;
+    st.tau = 0.0f;
+    if (n <= 0) return;
+    const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
+    const int32_t* ind = s.ind + oct * s.ind_oct;
+    int bprev = -1, slot = -1;
+    RecSample cur, nxt;
+    fetch_recorded(s, r, ind, krec[0], bprev, slot, cur);
+    for (int j = 0; j < n; ++j) {
+        if (j + 1 < n) fetch_recorded(s, r, ind, krec[j + 1], bprev, slot, nxt);
+        if (cur.slot >= 0) {
+            bool saturated;
+            const float wk = composite(s, cur.cv, cur.f, cur.g, st.T, st.tau, saturated);
+            scatter_sample(s, cur.slot, cur.fl, cur.o3, cur.f, cur.g, wk, gfeat, grad_atlas);
+        }
+        cur = nxt;
+    }
+}
+
 // MLP forward keeping the activations h1, h2 in the row; returns the sigmoid residual.
 __device__ __forceinline__ void mlp_forward_rows(const float* sW, float* row, float res[3]) {
     float h[16];

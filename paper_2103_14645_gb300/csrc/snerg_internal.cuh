@@ -591,45 +591,6 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
     st.steps = (int)steps;
 }
 
-// The adjoint scatter (march<..., GRAD>'s) of the n composited samples a march recorded
-// (REC), without the block entries and probes between them: each sample's block, stencil
-// and weight are recomputed exactly as the march computed them (the same lattice index,
-// the same binary32 control arithmetic, T and tau carried in the same order), so the
-// scattered values are those of a second march. T and tau after the last sample are left
-// in st for a march that continues from the next lattice index (CONT).
-__device__ __forceinline__ void scatter_recorded(const DevScene& s, const Ray& r, const int* krec, int n,
-                                                 const float* gfeat, float* grad_atlas, MarchState& st) {
-    st.T = 1.0f;
-    st.tau = 0.0f;
-    const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
-    const int32_t* ind = s.ind + oct * s.ind_oct;
-    int bprev = -1, slot = -1;
-    for (int j = 0; j < n; ++j) {
-        const float t = lattice_t(r, (float)krec[j]);
-        float u[3];
-        int b[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            u[i] = lattice_u(r, t, i);
-            b[i] = nearest_voxel(u[i], s.N) >> s.lgB;
-        }
-        const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
-        if (bi != bprev) {
-            slot = __ldg(ind + bi);
-            bprev = bi;
-        }
-        if (slot < 0) continue;     // not a block with samples: never recorded by a march
-        const float o3[3] = {(float)((b[0] << s.lgB) - 1), (float)((b[1] << s.lgB) - 1),
-                             (float)((b[2] << s.lgB) - 1)};
-        float f[3], g[3], fl[3];
-        uint2 cv[8];
-        load_stencil(u, o3, s.P, s.P3, s.patlas + (size_t)slot * s.P3, f, g, fl, cv);
-        bool saturated;
-        const float wk = composite(s, cv, f, g, st.T, st.tau, saturated);
-        scatter_sample(s, slot, fl, o3, f, g, wk, gfeat, grad_atlas);
-    }
-}
-
 // ---------------------------------------------------------------------------------
 // view-dependence MLP (Eq. 7): x = [C_d, V, d, sin/cos(2^l d), l = 0..3] -> 16 ReLU ->
 // 16 ReLU -> 3 -> sigmoid. Weights W come from shared memory (uniform broadcast reads).
