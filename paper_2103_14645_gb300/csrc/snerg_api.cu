@@ -573,7 +573,7 @@ extern "C" snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* ca
     if (n == 0) { delete t; return SNERG_OK; }
     if (!d_pix || !d_rgb || (!d_mlp && !h->has_w)) { delete t; return SNERG_E_INVAL; }
     cudaError_t e = launch_render_rays(h->ds, *t, n_cams, d_pix, n, d_mlp, d_mlp ? nullptr : &h->host_w, d_rgb,
-                                       make_dbg(opts), (cudaStream_t)stream);
+                                       make_dbg(opts), h->num_sms, (cudaStream_t)stream);
     delete t;
     if (e != cudaSuccess) return SNERG_E_CUDA;
     h->launches++;

@@ -198,12 +198,13 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW) render_image_kernel(const De
     }
 }
 
-template <bool DBG, bool PW>
-__global__ void __launch_bounds__(128, 8) render_rays_kernel(const DevScene s, const __grid_constant__ CamTable cams,
-                                                             int32_t n_cams, const int32_t* __restrict__ pix,
-                                                             int64_t n, const float* __restrict__ mlp,
-                                                             const __grid_constant__ MlpWeights pw,
-                                                             float* __restrict__ rgb, const DebugOut dbg) {
+// MINB: resident CTAs per SM the build is limited to (8: 64 registers; 4: up to 128)
+template <bool DBG, bool PW, int MINB>
+__global__ void __launch_bounds__(128, MINB) render_rays_kernel(const DevScene s, const __grid_constant__ CamTable cams,
+                                                                int32_t n_cams, const int32_t* __restrict__ pix,
+                                                                int64_t n, const float* __restrict__ mlp,
+                                                                const __grid_constant__ MlpWeights pw,
+                                                                float* __restrict__ rgb, const DebugOut dbg) {
     __shared__ __align__(16) float sW[PW ? 4 : kNParam + 1];
     if (!PW) {
         load_mlp_smem_t(sW, mlp);
@@ -341,20 +342,30 @@ cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
-                               int64_t n, const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg,
-                               cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
+template <int MINB>
+static void rays_launch(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
+                        const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg, cudaStream_t st) {
     const unsigned grid = (unsigned)((n + 127) / 128);
     const bool d = dbg.aux || dbg.counts || dbg.trace;
     const MlpWeights& w = pw ? *pw : no_weights();
     if (pw) {
-        if (d) render_rays_kernel<true, true><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
-        else render_rays_kernel<false, true><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
+        if (d) render_rays_kernel<true, true, MINB><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
+        else render_rays_kernel<false, true, MINB><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
     } else {
-        if (d) render_rays_kernel<true, false><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
-        else render_rays_kernel<false, false><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
+        if (d) render_rays_kernel<true, false, MINB><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
+        else render_rays_kernel<false, false, MINB><<<grid, 128, 0, st>>>(s, cams, n_cams, pix, n, mlp, w, rgb, dbg);
     }
+}
+
+// A ray list that fits one wave of 4 CTAs per SM runs the build limited to 4 (the march
+// keeps its state in registers, and a single wave gains nothing from the 8-CTA
+// occupancy); longer lists keep 8 CTAs per SM to hide the march's latencies.
+cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
+                               int64_t n, const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg,
+                               int num_sms, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if ((n + 127) / 128 <= 4 * (int64_t)num_sms) rays_launch<4>(s, cams, n_cams, pix, n, mlp, pw, rgb, dbg, st);
+    else rays_launch<8>(s, cams, n_cams, pix, n, mlp, pw, rgb, dbg, st);
     return cudaGetLastError();
 }
 

@@ -945,7 +945,7 @@ cudaError_t launch_render_image(const DevScene& s, const snerg_camera& cam, cons
                                 const SchedArgs* sch = nullptr);
 cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix,
                                int64_t n, const float* mlp, const MlpWeights* pw, float* rgb, const DebugOut& dbg,
-                               cudaStream_t st);
+                               int num_sms, cudaStream_t st);
 cudaError_t launch_backward_rays(const DevScene& s, const CamTable& cams, int32_t n_cams, const int32_t* pix, int64_t n,
                                  const float* mlp, const float* grad_rgb, const float* fwd_aux,
                                  const int32_t* fwd_counts, float* grad_atlas, float* grad_mlp, cudaStream_t st);

@@ -88,12 +88,17 @@ def test_forward_parity_paper_scale_view():
     np.testing.assert_array_equal(gt["counts"].cpu().numpy()[:, :2], ot["counts"])
 
 
-def test_rays_path_equals_image_path():
-    sc = scene("gauss64")
+@pytest.mark.parametrize("name", ["gauss64", "shell1024"])
+def test_rays_path_equals_image_path(name):
+    """Every pixel of the views as one ray list renders what the image launch renders, bit
+    for bit: 4,096 rays (one wave: the ray-list build limited to 4 CTAs per SM) and the
+    640,000 of the 800x800 view (the 8-CTA build)."""
+    sc = scene(name)
     g, r = gpu_render(sc)
     pix = synth.all_pixels(sc.cameras)
     w = torch.from_numpy(sc.mlp).to(DEV)
     rr = r.render_rays(sc.cameras, torch.from_numpy(pix).to(DEV), w).cpu().numpy()
+    r.check_status()
     np.testing.assert_array_equal(rr, g["rgb"])
 
 
