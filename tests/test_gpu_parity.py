@@ -597,6 +597,49 @@ def test_dense_grid_every_block_stored():
     assert_parity(g, oracle_all(sc, trace_cap=64))
 
 
+def _max_resolution_scene():
+    """N = 16384, the largest grid snerg_create accepts, in 64^3 blocks (G = 256): a 3 x 3 x 3
+    cluster of occupied blocks near the centre (5 % of their voxels with density, random
+    codes), and two views: a narrow one filled by the cluster, and a 39-degree one whose
+    rays cross the whole grid, nearly all of it empty."""
+    import math
+    N, B = 16384, 64
+    G = N // B
+    rng = np.random.default_rng(77)
+    ind = np.full((G, G, G), -1, np.int32)
+    c0 = G // 2 - 1
+    cells = [(z, y, x) for z in range(c0, c0 + 3) for y in range(c0, c0 + 3) for x in range(c0, c0 + 3)]
+    for i, (z, y, x) in enumerate(cells):
+        ind[z, y, x] = i
+    atl = rng.integers(0, 256, size=(len(cells), B, B, B, 8), dtype=np.uint8)
+    atl[..., 0] = np.where(rng.random((len(cells), B, B, B)) < 0.05, atl[..., 0], 0)
+    delta = synth.WORLD_EXTENT / N
+    centre = np.array(synth.WORLD_BMIN) + (c0 + 1.5) * B * delta
+    half = 1.5 * B * delta
+    pos = centre + synth.CAM_RADIUS * np.array([math.cos(0.4) * math.cos(0.7), math.cos(0.4) * math.sin(0.7),
+                                                math.sin(0.4)])
+    fov = 2.0 * math.degrees(math.atan(1.2 * half / synth.CAM_RADIUS))
+    narrow = synth.look_at_camera(pos, centre, 64, 64, fov)
+    wide = synth.orbit_cameras(rng, [(48, 40)], synth.CAM_RADIUS)[0]
+    cams = np.asarray([narrow, wide])
+    cams[1]["out_offset"] = 64 * 64
+    return synth.custom_scene(N, B, ind, atl, 2.0 / delta, synth.init_mlp(rng), cams)
+
+
+def test_maximum_grid_resolution():
+    """The largest grid (N = 16384: up to 28,000 lattice samples along a ray, block skips of
+    up to 32 blocks of 64 voxels): counts and visited voxels bit-exact, colours and
+    composites within 1e-4, against the oracle, for every pixel of both views."""
+    sc = _max_resolution_scene()
+    g, _ = gpu_render(sc, aux=True, counts=True, trace_cap=256)
+    o = oracle_all(sc, trace_cap=256)
+    assert o["counts"][:, 1].max() <= 256
+    assert (o["counts"][:4096, 1] > 0).sum() > 3000          # the narrow view sees the cluster
+    assert (o["aux"][:4096, 7] > 0.999).sum() > 100            # and some of its rays saturate
+    assert_parity(g, o)
+    assert g["counts"][4096:, 2].max() >= 8                    # wide-view rays cross the empty grid
+
+
 @pytest.mark.parametrize("sigma_vox", [1e-3, 200.0])
 def test_transparent_and_opaque_media(sigma_vox):
     """Nearly transparent (no ray saturates: every occupied sample is visited) and
