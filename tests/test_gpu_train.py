@@ -229,8 +229,9 @@ def test_train_rays_matches_oracle_and_the_separate_launches(flags):
 
 
 def test_finetuner_large_batch_takes_the_separate_launches():
-    """A batch larger than one wave of the adjoint kernel goes through render_rays ->
-    l2_loss -> backward; one step gives the same loss and weights as the fused launch."""
+    """A batch larger than the fused limit (8 waves of the adjoint kernel; forced here)
+    goes through render_rays -> l2_loss -> backward; one step gives the same loss and
+    weights as the fused launch."""
     sc = synth.make_scene("gauss64")
     rng = np.random.default_rng(19)
     pix_np = synth.random_pixels(rng, sc.cameras, 4096)
