@@ -3,12 +3,12 @@
 // colour and feature values, with density frozen).
 //
 // One thread per ray. The kernel marches the ray to get C_d, V, T and the MLP input
-// (recording the lattice indices of its first kRecCap composited samples), runs the MLP
-// adjoint in registers, then scatters w_k * (trilinear weight) * dL/d(C_d, V) into the
-// FP32 gradient atlas with vector atomics. Because density is frozen the composite
-// weights w_k depend only on the samples before k, so the scatter walks the recorded
-// samples in forward order, recomputing their weights, and marches on from the last
-// of them only for a ray that composited more. MLP weight gradients are
+// (recording the lattice index and weight w_k of its first kRecCap composited samples),
+// runs the MLP adjoint in registers, then scatters w_k * (trilinear weight) * dL/d(C_d, V)
+// into the FP32 gradient atlas with vector atomics. Because density is frozen the
+// composite weights w_k depend only on the samples before k, so the scatter walks the
+// recorded samples in forward order and marches on from the last of them only for a
+// ray that composited more. MLP weight gradients are
 // summed over the CTA's rays from activations staged in shared memory and reach global
 // memory with one atomic per parameter per CTA.
 #include <atomic>
@@ -27,61 +27,40 @@ constexpr int kMaxDevices = 64;     // transposed weights (883) rounded up to a 
 
 size_t backward_smem_bytes() { return (size_t)(kWFloats + kBwdThreads * kRow) * sizeof(float); }
 
-// One recorded sample's block slot, stencil and trilinear weights (march order: the
-// block of the sample's nearest voxel, its padded-atlas stencil).
-struct RecSample {
-    float o3[3], f[3], g[3], fl[3];
-    uint2 cv[8];
-    int slot;
-};
-
-__device__ __forceinline__ void fetch_recorded(const DevScene& s, const Ray& r, const int32_t* ind, int k,
-                                               int& bprev, int& slot, RecSample& x) {
-    const float t = lattice_t(r, (float)k);
-    float u[3];
-    int b[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        u[i] = lattice_u(r, t, i);
-        b[i] = nearest_voxel(u[i], s.N) >> s.lgB;
-    }
-    const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
-    if (bi != bprev) {
-        slot = __ldg(ind + bi);
-        bprev = bi;
-    }
-    x.slot = slot;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) x.o3[i] = (float)((b[i] << s.lgB) - 1);
-    // a block without samples is never recorded by a march; its slot only guards the address
-    load_stencil(u, x.o3, s.P, s.P3, s.patlas + (size_t)max(slot, 0) * s.P3, x.f, x.g, x.fl, x.cv);
-}
-
 // The adjoint scatter (march<..., GRAD>'s) of the n composited samples a march recorded
-// (REC), without the block entries and probes between them: each sample's block, stencil
-// and weight are recomputed exactly as the march computed them (the same lattice index,
-// the same binary32 control arithmetic, T and tau carried in the same order), so the
-// scattered values are those of a second march. The next sample's stencil is fetched
-// before the current one is composited, so that its latency overlaps. T and tau after the
-// last sample are left in st for a march that continues from the next lattice index (CONT).
-__device__ __forceinline__ void scatter_recorded(const DevScene& s, const Ray& r, const int* krec, int n,
+// (REC: each sample's lattice index and weight w_k), without the block entries and probes
+// between them and without reloading their stencils: each sample's block and trilinear
+// weights are recomputed from its lattice index as the march computed them, and w_k is
+// the march's own. T and tau after the kRecCap-th sample (rec[kRecCap]) go to st for a
+// march that continues from the next lattice index (CONT).
+__device__ __forceinline__ void scatter_recorded(const DevScene& s, const Ray& r, const float2* rec, int n,
                                                  const float* gfeat, float* grad_atlas, MarchState& st) {
-    st.T = 1.0f;
-    st.tau = 0.0f;
-    if (n <= 0) return;
     const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
     const int32_t* ind = s.ind + oct * s.ind_oct;
     int bprev = -1, slot = -1;
-    RecSample cur, nxt;
-    fetch_recorded(s, r, ind, krec[0], bprev, slot, cur);
     for (int j = 0; j < n; ++j) {
-        if (j + 1 < n) fetch_recorded(s, r, ind, krec[j + 1], bprev, slot, nxt);
-        if (cur.slot >= 0) {
-            bool saturated;
-            const float wk = composite(s, cur.cv, cur.f, cur.g, st.T, st.tau, saturated);
-            scatter_sample(s, cur.slot, cur.fl, cur.o3, cur.f, cur.g, wk, gfeat, grad_atlas);
+        const float2 e = rec[j];
+        const float t = lattice_t(r, e.x);
+        float u[3], o3[3], f[3], g[3], fl[3];
+        int b[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            u[i] = lattice_u(r, t, i);
+            b[i] = nearest_voxel(u[i], s.N) >> s.lgB;
+            o3[i] = (float)((b[i] << s.lgB) - 1);
         }
-        cur = nxt;
+        const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
+        if (bi != bprev) {
+            slot = __ldg(ind + bi);
+            bprev = bi;
+        }
+        if (slot < 0) continue;     // not a block with samples: never recorded by a march
+        stencil_weights(u, f, g, fl);
+        scatter_sample(s, slot, fl, o3, f, g, e.y, gfeat, grad_atlas);
+    }
+    if (n == kRecCap) {
+        st.T = rec[kRecCap].x;
+        st.tau = rec[kRecCap].y;
     }
 }
 
@@ -265,7 +244,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
     st.active = 0;
     st.T = 1.0f;
     int k_first = 0;
-    int krec[kRecCap];             // the first march's composited lattice indices
+    float2 rec[kRecCap + 1];       // the first march's composited samples (index, w_k), then T, tau
     if (i < n) {
         const int ci = __ldg(pix + 3 * i), px = __ldg(pix + 3 * i + 1), py = __ldg(pix + 3 * i + 2);
         if (ci >= 0 && ci < n_cams && px >= 0 && py >= 0 && px < cams.c[ci].W && py < cams.c[ci].H)
@@ -280,7 +259,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
             for (int c = 0; c < 7; ++c) st.acc[c] = __ldg(fwd_aux + kAuxCh * i + c) * 255.0f;
         } else {
             march<false, false, false, true, true>(s, r, st, nullptr, 0, nullptr, nullptr, 0, &k_first, nullptr,
-                                                   nullptr, krec);
+                                                   nullptr, rec);
             record_status(s, st);
         }
     }
@@ -367,11 +346,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
         for (int c = 0; c < 4; ++c) gf[3 + c] = sc * gx[3 + c];
         MarchState st2;
         if (!STATE) {
-            scatter_recorded(s, r, krec, min(st.active, kRecCap), gf, grad_atlas, st2);
+            scatter_recorded(s, r, rec, min(st.active, kRecCap), gf, grad_atlas, st2);
             // a ray with more composited samples marches on from the last recorded one
             if (st.active > kRecCap)
                 march<false, true, false, true, false, true>(s, r, st2, nullptr, 0, gf, grad_atlas,
-                                                             krec[kRecCap - 1] + 1);
+                                                             (int)rec[kRecCap - 1].x + 1);
         } else {
             // without a recording (the forward's per-ray state given) a second march starts
             // at the first composited sample: nothing before it contributes (T = 1 and

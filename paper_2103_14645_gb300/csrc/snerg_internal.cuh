@@ -322,8 +322,7 @@ __device__ __forceinline__ void accumulate_colour(MarchState& st, const uint2 cv
 // codes (index z*4 + y*2 + x). The lower corner is in [0, B] for a sample of this block
 // (the apron holds the neighbours and the clamped border); the index clamp only guards
 // the address.
-__device__ __forceinline__ void load_stencil(const float u[3], const float o[3], int P, int P3, const uint2* pa,
-                                             float f[3], float g[3], float fl[3], uint2 cv[8]) {
+__device__ __forceinline__ void stencil_weights(const float u[3], float f[3], float g[3], float fl[3]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float x = __fsub_rn(u[i], 0.5f);
@@ -331,6 +330,11 @@ __device__ __forceinline__ void load_stencil(const float u[3], const float o[3],
         f[i] = __fsub_rn(x, fl[i]);
         g[i] = __fsub_rn(1.0f, f[i]);
     }
+}
+
+__device__ __forceinline__ void load_stencil(const float u[3], const float o[3], int P, int P3, const uint2* pa,
+                                             float f[3], float g[3], float fl[3], uint2 cv[8]) {
+    stencil_weights(u, f, g, fl);
     const int PP = P * P;
     const float Pf = (float)P;
     const int i0 = min(max((int)fmaf(fmaf(fl[2] - o[2], Pf, fl[1] - o[1]), Pf, fl[0] - o[0]), 0), P3 - 1 - (PP + P + 1));
@@ -419,14 +423,16 @@ __device__ __forceinline__ void scatter_sample(const DevScene& s, int slot, cons
     }
 }
 
-// Composited samples a march records (REC) for the adjoint's scatter
+// Composited samples a march records (REC) for the adjoint's scatter: (lattice index, w_k)
+// of each of the first kRecCap, then (T, tau) after the last of them
 constexpr int kRecCap = 32;
 
 // ---------------------------------------------------------------------------------
 // the march. TRACE records visited voxels; GRAD scatters w_k * trilinear weight * g
 // into the gradient atlas (density frozen, so the weights are the forward ones); REC
-// stores the lattice indices of the first kRecCap composited samples in krec; CONT
-// starts from the T and tau already in st (a march resumed after recorded samples).
+// stores the lattice index and weight of the first kRecCap composited samples in rec[j]
+// and T, tau after them in rec[kRecCap]; CONT starts from the T and tau already in st (a
+// march resumed after recorded samples).
 // ---------------------------------------------------------------------------------
 // k_begin: first lattice index to consider (0, or a k known to precede every composited
 // sample, in which case the result is the same); k_first (nullable) receives the index
@@ -444,7 +450,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                                       const float* gfeat, float* grad_atlas,
                                       int k_begin = 0, int* k_first = nullptr,
                                       const MlpWeights* ps_w = nullptr, const float* ps_sw = nullptr,
-                                      int* krec = nullptr) {
+                                      float2* rec = nullptr) {
 #pragma unroll
     for (int c = 0; c < 7; ++c) st.acc[c] = 0.0f;
     st.rgb_ps[0] = st.rgb_ps[1] = st.rgb_ps[2] = 0.0f;
@@ -546,12 +552,15 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 trace[st.active] = ((uint64_t)nearest_voxel(u[2], N) * N + (uint64_t)nearest_voxel(u[1], N)) * N +
                                    (uint64_t)nearest_voxel(u[0], N);
             if (k_first && st.active == 0) *k_first = (int)kk;
-            if (REC && st.active < kRecCap) krec[st.active] = (int)kk;
             st.active++;
             // trilinear stencil on the virtual grid, cell-centred
             if (!spec) load_stencil(u, o3, P, s.P3, pa, f, g, fl, cv);
             bool saturated;
             const float wk = composite(s, cv, f, g, st.T, st.tau, saturated);
+            if (REC && st.active <= kRecCap) {
+                rec[st.active - 1] = make_float2(kk, wk);
+                if (st.active == kRecCap) rec[kRecCap] = make_float2(st.T, st.tau);
+            }
             accumulate_colour(st, cv, wk, f, g);
             if (PS) {
                 // this sample's own decoded colour and features, then its residual
