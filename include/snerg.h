@@ -223,8 +223,10 @@ snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* cams, int32_t
                                float* d_rgb, const snerg_render_opts* opts, void* stream);
 
 /* Adjoint of snerg_render_rays for an upstream gradient d_grad_rgb [n][3] = dL/dC
- * (Sec. 5.5 fine-tunes against an L2 image loss, Eq. 3). Density is frozen. Nothing
- * per sample is stored: each ray is marched again. ACCUMULATES (caller zeroes):
+ * (Sec. 5.5 fine-tunes against an L2 image loss, Eq. 3). Density is frozen. No
+ * per-sample state passes between calls: the kernel marches each ray itself (keeping its
+ * first 32 composited samples' lattice indices and weights for its own scatter).
+ * ACCUMULATES (caller zeroes):
  *   d_grad_atlas : float32 [num_blocks][B][B][B][8], dL/d(q/255) of channels 1..7 of
  *                  every stored voxel; channel 0 (density) receives exactly zero;
  *   d_grad_mlp   : float32 [SNERG_MLP_PARAMS].
@@ -232,8 +234,8 @@ snerg_status snerg_render_rays(snerg_handle h, const snerg_camera* cams, int32_t
  * d_fwd_aux / d_fwd_counts (both or neither, nullable): the opts.d_aux and
  * opts.d_counts outputs of the snerg_render_rays call that produced C for these rays with
  * the same cameras, rays and weights. Given them, the kernel takes C_d, V and the first
- * composited lattice index from them (per-ray state, 9 words) instead of marching the
- * ray twice; the gradients are the same. */
+ * composited lattice index from them (per-ray state, 9 words) instead of its own first
+ * march, and scatters with one march from that index; the gradients are the same. */
 snerg_status snerg_render_backward(snerg_handle h, const snerg_camera* cams, int32_t n_cams,
                                    const int32_t* d_pix, int64_t n, const float* d_mlp,
                                    const float* d_grad_rgb, const float* d_fwd_aux,

@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) backward_rays_kernel(
             }
         }
     }
-    // the atlas scatter before the CTA's barrier: each ray's second march follows its own
-    // first one instead of waiting for the CTA's slowest first march
+    // the atlas scatter before the CTA's barrier: each ray's scatter follows its own first
+    // march instead of waiting for the CTA's slowest one
     if (active && grad_atlas) {
         float gf[7];
 #pragma unroll
