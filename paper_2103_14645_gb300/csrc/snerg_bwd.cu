@@ -38,8 +38,10 @@ __device__ __forceinline__ void scatter_recorded(const DevScene& s, const Ray& r
     const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
     const int32_t* ind = s.ind + oct * s.ind_oct;
     int bprev = -1, slot = -1;
+    float2 nx = n > 0 ? rec[0] : make_float2(0.0f, 0.0f);
     for (int j = 0; j < n; ++j) {
-        const float2 e = rec[j];
+        const float2 e = nx;
+        if (j + 1 < n) nx = rec[j + 1];     // the next record's load overlaps this sample
         const float t = lattice_t(r, e.x);
         float u[3], o3[3], f[3], g[3], fl[3];
         int b[3];
