@@ -27,38 +27,61 @@ constexpr int kMaxDevices = 64;     // transposed weights (883) rounded up to a 
 
 size_t backward_smem_bytes() { return (size_t)(kWFloats + kBwdThreads * kRow) * sizeof(float); }
 
+// A recorded sample's lattice position, block origin (minus one), block slot and weight.
+struct RecSample {
+    float u[3], o3[3], w;
+    int slot;
+};
+
+__device__ __forceinline__ void locate_recorded(const DevScene& s, const Ray& r, const int32_t* ind, float2 e,
+                                                int& bprev, int& slot, RecSample& x) {
+    const float t = lattice_t(r, e.x);
+    int b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        x.u[i] = lattice_u(r, t, i);
+        b[i] = nearest_voxel(x.u[i], s.N) >> s.lgB;
+        x.o3[i] = (float)((b[i] << s.lgB) - 1);
+    }
+    const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
+    if (bi != bprev) {
+        slot = __ldg(ind + bi);
+        bprev = bi;
+    }
+    x.slot = slot;
+    x.w = e.y;
+}
+
 // The adjoint scatter (march<..., GRAD>'s) of the n composited samples a march recorded
 // (REC: each sample's lattice index and weight w_k), without the block entries and probes
 // between them and without reloading their stencils: each sample's block and trilinear
 // weights are recomputed from its lattice index as the march computed them, and w_k is
-// the march's own. T and tau after the kRecCap-th sample (rec[kRecCap]) go to st for a
-// march that continues from the next lattice index (CONT).
+// the march's own. The next sample is located (its record and, on a block change, its
+// slot loaded) before the current one's atomics, so that those loads overlap them. T and
+// tau after the kRecCap-th sample (rec[kRecCap]) go to st for a march that continues from
+// the next lattice index (CONT).
 __device__ __forceinline__ void scatter_recorded(const DevScene& s, const Ray& r, const float2* rec, int n,
                                                  const float* gfeat, float* grad_atlas, MarchState& st) {
-    const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
-    const int32_t* ind = s.ind + oct * s.ind_oct;
-    int bprev = -1, slot = -1;
-    float2 nx = n > 0 ? rec[0] : make_float2(0.0f, 0.0f);
-    for (int j = 0; j < n; ++j) {
-        const float2 e = nx;
-        if (j + 1 < n) nx = rec[j + 1];     // the next record's load overlaps this sample
-        const float t = lattice_t(r, e.x);
-        float u[3], o3[3], f[3], g[3], fl[3];
-        int b[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            u[i] = lattice_u(r, t, i);
-            b[i] = nearest_voxel(u[i], s.N) >> s.lgB;
-            o3[i] = (float)((b[i] << s.lgB) - 1);
+    if (n > 0) {
+        const int oct = (r.d[0] < 0.0f ? 1 : 0) | (r.d[1] < 0.0f ? 2 : 0) | (r.d[2] < 0.0f ? 4 : 0);
+        const int32_t* ind = s.ind + oct * s.ind_oct;
+        int bprev = -1, slot = -1;
+        RecSample cur, nxt;
+        locate_recorded(s, r, ind, rec[0], bprev, slot, cur);
+        float2 e = n > 1 ? rec[1] : make_float2(0.0f, 0.0f);
+        for (int j = 0; j < n; ++j) {
+            if (j + 1 < n) {
+                locate_recorded(s, r, ind, e, bprev, slot, nxt);
+                if (j + 2 < n) e = rec[j + 2];
+            }
+            // a block without samples is never recorded by a march
+            if (cur.slot >= 0) {
+                float f[3], g[3], fl[3];
+                stencil_weights(cur.u, f, g, fl);
+                scatter_sample(s, cur.slot, fl, cur.o3, f, g, cur.w, gfeat, grad_atlas);
+            }
+            cur = nxt;
         }
-        const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
-        if (bi != bprev) {
-            slot = __ldg(ind + bi);
-            bprev = bi;
-        }
-        if (slot < 0) continue;     // not a block with samples: never recorded by a march
-        stencil_weights(u, f, g, fl);
-        scatter_sample(s, slot, fl, o3, f, g, e.y, gfeat, grad_atlas);
     }
     if (n == kRecCap) {
         st.T = rec[kRecCap].x;
