@@ -403,7 +403,7 @@ static snerg_status render_persistent(snerg_scene* h, const snerg_camera* cams, 
     const MlpWeights* w_arg = pw ? pw : &zero_w;
     void* args[] = {(void*)&ds, (void*)p, (void*)&mlp_arg, (void*)w_arg, (void*)&rgb_arg, (void*)&queue};
     cudaKernelNodeParams kp = {};
-    kp.func = const_cast<void*>(persistent_kernel_fn(pw != nullptr));
+    kp.func = const_cast<void*>(persistent_kernel_fn(pw != nullptr, cfg.passes > 1));
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(cfg.block);
     kp.sharedMemBytes = 0;

@@ -249,7 +249,27 @@ __global__ void __launch_bounds__(128, MINB) render_rays_kernel(const DevScene s
 // (tile_w x tile_h pixels of one camera) from a global counter until the queue is empty,
 // and renders each item in warp_w x warp_h packets of 32 rays. The counter is zeroed by
 // the launch sequence (a memset node of the captured graph) before every launch.
+// One pixel of the persistent launch: march, shade and store.
 template <bool PW>
+__device__ __forceinline__ void persistent_pixel(const DevScene& s, const snerg_camera& cam, const float* sW,
+                                                 const MlpWeights& pw, float* rgb, int px, int py) {
+    // the output row before the march, so that only it stays live across it
+    float* out = rgb + (cam.out_offset + (int64_t)py * cam.W + px) * 3;
+    const Ray r = make_ray(s, cam, px, py);
+    MarchState st;
+    march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
+    record_status(s, st);
+    float c[3], aux[kAuxCh];
+    finish_ray(s, sW, nullptr, r, st, c, aux, PW ? &pw : nullptr);
+    out[0] = c[0];
+    out[1] = c[1];
+    out[2] = c[2];
+}
+
+// MULTI: a work item is several warp passes (tile_w x tile_h larger than warp_w x
+// warp_h); without it an item is exactly one warp pass and no pass loop stays live across
+// the march.
+template <bool PW, bool MULTI>
 __global__ void __launch_bounds__(128, 8) render_persistent_kernel(const DevScene s,
                                                                    const __grid_constant__ PersistentParams p,
                                                                    const float* __restrict__ mlp,
@@ -262,9 +282,6 @@ __global__ void __launch_bounds__(128, 8) render_persistent_kernel(const DevScen
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const int passes_x = p.tile_w / p.warp_w;
-    const int passes = passes_x * (p.tile_h / p.warp_h);
-    const int lx = lane % p.warp_w, ly = lane / p.warp_w;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(queue, 1);
@@ -278,21 +295,19 @@ __global__ void __launch_bounds__(128, 8) render_persistent_kernel(const DevScen
         const snerg_camera& cam = p.cams[lo];
         const int rem = item - p.tile_start[lo];
         const int tx = rem % p.tiles_x[lo], ty = rem / p.tiles_x[lo];
-        for (int ps = 0; ps < passes; ++ps) {
-            const int px = tx * p.tile_w + (ps % passes_x) * p.warp_w + lx;
-            const int py = ty * p.tile_h + (ps / passes_x) * p.warp_h + ly;
-            if (px < cam.W && py < cam.H) {
-                const Ray r = make_ray(s, cam, px, py);
-                MarchState st;
-                march<false, false>(s, r, st, nullptr, 0, nullptr, nullptr);
-                record_status(s, st);
-                float c[3], aux[kAuxCh];
-                finish_ray(s, sW, nullptr, r, st, c, aux, PW ? &pw : nullptr);
-                const int64_t o = (cam.out_offset + (int64_t)py * cam.W + px) * 3;
-                rgb[o + 0] = c[0];
-                rgb[o + 1] = c[1];
-                rgb[o + 2] = c[2];
+        const int lx = lane % p.warp_w, ly = lane / p.warp_w;
+        if (MULTI) {
+            const int passes_x = p.tile_w / p.warp_w;
+            const int passes = passes_x * (p.tile_h / p.warp_h);
+            for (int ps = 0; ps < passes; ++ps) {
+                const int px = tx * p.tile_w + (ps % passes_x) * p.warp_w + lx;
+                const int py = ty * p.tile_h + (ps / passes_x) * p.warp_h + ly;
+                if (px < cam.W && py < cam.H) persistent_pixel<PW>(s, cam, sW, pw, rgb, px, py);
             }
+        } else {
+            const int px = tx * p.warp_w + lx;
+            const int py = ty * p.warp_h + ly;
+            if (px < cam.W && py < cam.H) persistent_pixel<PW>(s, cam, sW, pw, rgb, px, py);
         }
     }
 }
@@ -369,16 +384,21 @@ cudaError_t launch_render_rays(const DevScene& s, const CamTable& cams, int32_t 
     return cudaGetLastError();
 }
 
+static bool persistent_multi(const PersistentParams& p) { return p.tile_w != p.warp_w || p.tile_h != p.warp_h; }
+
 cudaError_t launch_render_persistent(const DevScene& s, const PersistentParams& p, const float* mlp,
                                      const MlpWeights* pw, float* rgb, int32_t* queue, int grid, int block,
                                      cudaStream_t st) {
-    if (pw) render_persistent_kernel<true><<<grid, block, 0, st>>>(s, p, mlp, *pw, rgb, queue);
-    else render_persistent_kernel<false><<<grid, block, 0, st>>>(s, p, mlp, no_weights(), rgb, queue);
-    return cudaGetLastError();
+    const void* fn = persistent_kernel_fn(pw != nullptr, persistent_multi(p));
+    const MlpWeights& w = pw ? *pw : no_weights();
+    void* args[] = {(void*)&s, (void*)&p, (void*)&mlp, (void*)&w, (void*)&rgb, (void*)&queue};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, st);
 }
 
-const void* persistent_kernel_fn(bool param_weights) {
-    return param_weights ? (const void*)render_persistent_kernel<true> : (const void*)render_persistent_kernel<false>;
+const void* persistent_kernel_fn(bool param_weights, bool multi) {
+    if (param_weights)
+        return multi ? (const void*)render_persistent_kernel<true, true> : (const void*)render_persistent_kernel<true, false>;
+    return multi ? (const void*)render_persistent_kernel<false, true> : (const void*)render_persistent_kernel<false, false>;
 }
 
 }  // namespace snerg

@@ -987,6 +987,8 @@ struct PersistentParams {
 cudaError_t launch_render_persistent(const DevScene& s, const PersistentParams& p, const float* mlp,
                                      const MlpWeights* pw, float* rgb, int32_t* queue, int grid, int block,
                                      cudaStream_t st);
-const void* persistent_kernel_fn(bool param_weights);
+// the persistent kernel for weights as parameters or in device memory, and for work items
+// of one warp pass or several (multi)
+const void* persistent_kernel_fn(bool param_weights, bool multi);
 
 }  // namespace snerg
