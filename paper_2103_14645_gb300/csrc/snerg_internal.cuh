@@ -602,59 +602,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
 
 // ---------------------------------------------------------------------------------
 // view-dependence MLP (Eq. 7): x = [C_d, V, d, sin/cos(2^l d), l = 0..3] -> 16 ReLU ->
-// 16 ReLU -> 3 -> sigmoid. Weights W come from shared memory (uniform broadcast reads).
-// ---------------------------------------------------------------------------------
-__device__ __forceinline__ void mlp_input(const float cd[3], const float v[4], const float d[3], float x[kMlpIn]) {
-    x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
-    x[3] = v[0]; x[4] = v[1]; x[5] = v[2]; x[6] = v[3];
-    x[7] = d[0]; x[8] = d[1]; x[9] = d[2];
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            float sv, cv;
-            sincosf((float)(1 << l) * d[i], &sv, &cv);
-            x[10 + 6 * l + i] = sv;
-            x[13 + 6 * l + i] = cv;
-        }
-    }
-}
-
-struct MlpAct {
-    float h1[kMlpH], h2[kMlpH], res[kMlpOut];
-};
-
-__device__ __forceinline__ void mlp_forward(const float* W, const float x[kMlpIn], MlpAct& a) {
-#pragma unroll
-    for (int o = 0; o < kMlpH; ++o) {
-        float acc = W[kOffB1 + o];
-#pragma unroll
-        for (int i = 0; i < kMlpIn; ++i) acc = fmaf(W[kOffW1 + o * kMlpIn + i], x[i], acc);
-        a.h1[o] = fmaxf(acc, 0.0f);
-    }
-#pragma unroll
-    for (int o = 0; o < kMlpH; ++o) {
-        float acc = W[kOffB2 + o];
-#pragma unroll
-        for (int i = 0; i < kMlpH; ++i) acc = fmaf(W[kOffW2 + o * kMlpH + i], a.h1[i], acc);
-        a.h2[o] = fmaxf(acc, 0.0f);
-    }
-#pragma unroll
-    for (int o = 0; o < kMlpOut; ++o) {
-        float acc = W[kOffB3 + o];
-#pragma unroll
-        for (int i = 0; i < kMlpH; ++i) acc = fmaf(W[kOffW3 + o * kMlpH + i], a.h2[i], acc);
-        a.res[o] = 1.0f / (1.0f + expf(-acc));
-    }
-}
-
-__device__ __forceinline__ void load_mlp_smem(float* sW, const float* mlp) {
-    for (int i = threadIdx.x + threadIdx.y * blockDim.x; i < kNParam; i += blockDim.x * blockDim.y)
-        sW[i] = __ldg(mlp + i);
-}
-
-// ---------------------------------------------------------------------------------
-// Forward-kernel form of the same MLP, built to stay small in registers and code:
+// 16 ReLU -> 3 -> sigmoid, built to stay small in registers and code:
 // weights sit in shared memory with W1 and W2 transposed (rows of 16 outputs, read with
 // uniform 128-bit loads), the 34-float input row of each thread is staged in shared
 // memory and streamed through a rolled loop, and the direction encoding takes one
