@@ -164,8 +164,21 @@ __device__ __forceinline__ float lattice_u(const Ray& r, float t, int i) {
     return __fadd_rn(r.o[i], __fmul_rn(t, r.d[i]));
 }
 
+// Floor, ceiling and integer value of a binary32 x with |x| < 2^22, on the FMA and
+// integer pipes instead of the conversion unit: x + 1.5 * 2^23 lies in [2^23, 2^24),
+// where the spacing of binary32 is 1, so that sum rounded down (up) is 1.5 * 2^23 plus
+// floor(x) (ceil(x)) exactly, and its bit pattern is 0x4B400000 plus that integer. The
+// results are exactly floorf / ceilf / the conversion of an integral x.
+constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+__device__ __forceinline__ float floor_small(float x) { return __fsub_rn(__fadd_rd(x, kMagic), kMagic); }
+__device__ __forceinline__ float ceil_small(float x) { return __fsub_rn(__fadd_ru(x, kMagic), kMagic); }
+__device__ __forceinline__ int floor_int_small(float x) { return __float_as_int(__fadd_rd(x, kMagic)) - kMagicBits; }
+__device__ __forceinline__ int int_small(float x) { return __float_as_int(__fadd_rn(x, kMagic)) - kMagicBits; }
+
+// a lattice coordinate lies within the grid up to rounding (|u| <= N + 1 <= 16385)
 __device__ __forceinline__ int nearest_voxel(float u, int N) {
-    return min(max((int)floorf(u), 0), N - 1);
+    return min(max(floor_int_small(u), 0), N - 1);
 }
 
 // A box of blocks lo..hi (inclusive, per axis) as bounds on the sample position: the
@@ -242,7 +255,7 @@ __device__ __forceinline__ float box_exit(const Ray& r, const float inv_d[3], fl
         else if (r.d[i] < 0.0f) te = fminf(te, (bx.lo[i] - r.o[i]) * inv_d[i]);
     }
     const float K = te - r.t0 - 0.5f;
-    const float n = ceilf(K);
+    const float n = ceil_small(K);        // |K| <= t1 - t0 + 1 (or NaN, kept)
     // fr in [0, 1). n - K is exact for K >= 1/2 (Sterbenz) and for K <= 0; for K in
     // (0, 1/2), n = 1 and 1 - K rounds by at most 2^-25, far inside the margin (at least
     // 4 * 2^-20, four times the bound on the estimate's own error), so the test below
@@ -326,7 +339,7 @@ __device__ __forceinline__ void stencil_weights(const float u[3], float f[3], fl
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float x = __fsub_rn(u[i], 0.5f);
-        fl[i] = floorf(x);
+        fl[i] = floor_small(x);
         f[i] = __fsub_rn(x, fl[i]);
         g[i] = __fsub_rn(1.0f, f[i]);
     }
@@ -337,7 +350,8 @@ __device__ __forceinline__ void load_stencil(const float u[3], const float o[3],
     stencil_weights(u, f, g, fl);
     const int PP = P * P;
     const float Pf = (float)P;
-    const int i0 = min(max((int)fmaf(fmaf(fl[2] - o[2], Pf, fl[1] - o[1]), Pf, fl[0] - o[0]), 0), P3 - 1 - (PP + P + 1));
+    const int i0 = min(max(int_small(fmaf(fmaf(fl[2] - o[2], Pf, fl[1] - o[1]), Pf, fl[0] - o[0])), 0),
+                       P3 - 1 - (PP + P + 1));
     const uint2* p0 = pa + i0;
     cv[0] = __ldg(p0);
     cv[1] = __ldg(p0 + 1);
@@ -408,9 +422,9 @@ __device__ __forceinline__ void scatter_sample(const DevScene& s, int slot, cons
     } else {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int X = min(max((int)fl[0] + (c & 1), 0), N - 1);
-            const int Y = min(max((int)fl[1] + ((c >> 1) & 1), 0), N - 1);
-            const int Z = min(max((int)fl[2] + ((c >> 2) & 1), 0), N - 1);
+            const int X = min(max(int_small(fl[0]) + (c & 1), 0), N - 1);
+            const int Y = min(max(int_small(fl[1]) + ((c >> 1) & 1), 0), N - 1);
+            const int Z = min(max(int_small(fl[2]) + ((c >> 2) & 1), 0), N - 1);
             const int cs = __ldg(s.ind + (((Z >> s.lgB) * s.G + (Y >> s.lgB)) * s.G + (X >> s.lgB)));
             if (cs < 0) continue;
             const int loc = (((Z & (B - 1)) * B) + (Y & (B - 1))) * B + (X & (B - 1));
@@ -527,8 +541,8 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             // grid -- apron cells that hold the clamped edge voxel's value (the grid clamp
             // is built into the plane); small integers, exact in binary32. The index clamp
             // only guards the address.
-            const float lx = floorf(u[0]) - ox, ly = floorf(u[1]) - oy, lz = floorf(u[2]) - oz;
-            const int pidx = min(max((int)fmaf(fmaf(lz, Pf, ly), Pf, lx), 0), s.P3 - 1);
+            const float lx = floor_small(u[0]) - ox, ly = floor_small(u[1]) - oy, lz = floor_small(u[2]) - oz;
+            const int pidx = min(max(int_small(fmaf(fmaf(lz, Pf, ly), Pf, lx)), 0), s.P3 - 1);
             // SPEC: the sample's stencil is loaded before the probe's answer when the
             // previous sample was composited (inside a surface the next one usually is
             // too, and one memory latency then serves both), after it otherwise. It pays
@@ -545,7 +559,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 // has density: the next s_max samples (s_max*m + eps < vd - 1) are empty,
                 // skip them
                 const float q = ((float)vd - 1.0f - skip_eps) * skip_inv_m;
-                kk += fmaxf(1.0f, ceilf(q));      // = 1 + s_max, s_max = ceil(q) - 1 >= 0
+                kk += fmaxf(1.0f, ceil_small(q));      // = 1 + s_max, s_max = ceil(q) - 1 >= 0
                 continue;
             }
             if (TRACE && st.active < trace_cap)
