@@ -175,6 +175,8 @@ __device__ __forceinline__ float floor_small(float x) { return __fsub_rn(__fadd_
 __device__ __forceinline__ float ceil_small(float x) { return __fsub_rn(__fadd_ru(x, kMagic), kMagic); }
 __device__ __forceinline__ int floor_int_small(float x) { return __float_as_int(__fadd_rd(x, kMagic)) - kMagicBits; }
 __device__ __forceinline__ int int_small(float x) { return __float_as_int(__fadd_rn(x, kMagic)) - kMagicBits; }
+// and back: the binary32 value of an integer |v| < 2^22
+__device__ __forceinline__ float float_small(int v) { return __fsub_rn(__int_as_float(v + kMagicBits), kMagic); }
 
 // a lattice coordinate lies within the grid up to rounding (|u| <= N + 1 <= 16385)
 __device__ __forceinline__ int nearest_voxel(float u, int N) {
@@ -195,8 +197,8 @@ __device__ __forceinline__ Box make_box(const DevScene& s, const int lo[3], cons
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const int L = lo[i] * s.B, H = (hi[i] + 1) * s.B;
-        bx.lo[i] = L <= 0 ? -INFINITY : (float)L;
-        bx.hi[i] = H >= s.N ? INFINITY : (float)H;
+        bx.lo[i] = L <= 0 ? -INFINITY : float_small(L);       // block corners: 0 < L, H < N <= 16384
+        bx.hi[i] = H >= s.N ? INFINITY : float_small(H);
     }
     return bx;
 }
@@ -527,8 +529,8 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
         const uint8_t* vs = vskip + (size_t)slot * s.P3;
         const uint2* pa = s.patlas + (size_t)slot * s.P3;
         // block origin minus one, so that the padded local coordinate is floor(u) - o
-        const float ox = (float)((b[0] << s.lgB) - 1), oy = (float)((b[1] << s.lgB) - 1),
-                    oz = (float)((b[2] << s.lgB) - 1);
+        const float ox = float_small((b[0] << s.lgB) - 1), oy = float_small((b[1] << s.lgB) - 1),
+                    oz = float_small((b[2] << s.lgB) - 1);
         const float Pf = (float)P;
         float kk = k;
         while (kk < kx) {
@@ -558,7 +560,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
                 // no voxel of this block in the ray's cone within Chebyshev distance vd-1
                 // has density: the next s_max samples (s_max*m + eps < vd - 1) are empty,
                 // skip them
-                const float q = ((float)vd - 1.0f - skip_eps) * skip_inv_m;
+                const float q = (float_small(vd) - 1.0f - skip_eps) * skip_inv_m;
                 kk += fmaxf(1.0f, ceil_small(q));      // = 1 + s_max, s_max = ceil(q) - 1 >= 0
                 continue;
             }
