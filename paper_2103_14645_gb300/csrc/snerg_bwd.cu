@@ -29,7 +29,8 @@ size_t backward_smem_bytes() { return (size_t)(kWFloats + kBwdThreads * kRow) * 
 
 // A recorded sample's lattice position, block origin (minus one), block slot and weight.
 struct RecSample {
-    float u[3], o3[3], w;
+    float u[3], w;
+    int o3[3];
     int slot;
 };
 
@@ -41,7 +42,7 @@ __device__ __forceinline__ void locate_recorded(const DevScene& s, const Ray& r,
     for (int i = 0; i < 3; ++i) {
         x.u[i] = lattice_u(r, t, i);
         b[i] = nearest_voxel(x.u[i], s.N) >> s.lgB;
-        x.o3[i] = (float)((b[i] << s.lgB) - 1);
+        x.o3[i] = (b[i] << s.lgB) - 1;
     }
     const int bi = (b[2] * s.G + b[1]) * s.G + b[0];
     if (bi != bprev) {
@@ -77,8 +78,9 @@ __device__ __forceinline__ void scatter_recorded(const DevScene& s, const Ray& r
             // a block without samples is never recorded by a march
             if (cur.slot >= 0) {
                 float f[3], g[3], fl[3];
-                stencil_weights(cur.u, f, g, fl);
-                scatter_sample(s, cur.slot, fl, cur.o3, f, g, cur.w, gfeat, grad_atlas);
+                int fi[3];
+                stencil_weights(cur.u, f, g, fl, fi);
+                scatter_sample(s, cur.slot, fi, cur.o3, f, g, cur.w, gfeat, grad_atlas);
             }
             cur = nxt;
         }

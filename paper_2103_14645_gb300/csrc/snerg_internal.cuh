@@ -333,27 +333,28 @@ __device__ __forceinline__ void accumulate_colour(MarchState& st, const uint2 cv
 }
 
 // The trilinear stencil of a sample at u in block-padded coordinates (block origin minus
-// one at o): the fractional weights f, g = 1 - f, the lower corner fl, and the 8 corners'
+// one at o, integer voxel coordinates): the fractional weights f, g = 1 - f, the lower
+// corner (as the float fl and the integer fi, both from one add), and the 8 corners'
 // codes (index z*4 + y*2 + x). The lower corner is in [0, B] for a sample of this block
 // (the apron holds the neighbours and the clamped border); the index clamp only guards
 // the address.
-__device__ __forceinline__ void stencil_weights(const float u[3], float f[3], float g[3], float fl[3]) {
+__device__ __forceinline__ void stencil_weights(const float u[3], float f[3], float g[3], float fl[3], int fi[3]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const float x = __fsub_rn(u[i], 0.5f);
-        fl[i] = floor_small(x);
+        const float m = __fadd_rd(x, kMagic);            // floor_small / floor_int_small of x
+        fl[i] = __fsub_rn(m, kMagic);
+        fi[i] = __float_as_int(m) - kMagicBits;
         f[i] = __fsub_rn(x, fl[i]);
         g[i] = __fsub_rn(1.0f, f[i]);
     }
 }
 
-__device__ __forceinline__ void load_stencil(const float u[3], const float o[3], int P, int P3, const uint2* pa,
-                                             float f[3], float g[3], float fl[3], uint2 cv[8]) {
-    stencil_weights(u, f, g, fl);
+__device__ __forceinline__ void load_stencil(const float u[3], const int o[3], int P, int P3, const uint2* pa,
+                                             float f[3], float g[3], float fl[3], int fi[3], uint2 cv[8]) {
+    stencil_weights(u, f, g, fl, fi);
     const int PP = P * P;
-    const float Pf = (float)P;
-    const int i0 = min(max(int_small(fmaf(fmaf(fl[2] - o[2], Pf, fl[1] - o[1]), Pf, fl[0] - o[0])), 0),
-                       P3 - 1 - (PP + P + 1));
+    const int i0 = min(max(((fi[2] - o[2]) * P + (fi[1] - o[1])) * P + (fi[0] - o[0]), 0), P3 - 1 - (PP + P + 1));
     const uint2* p0 = pa + i0;
     cv[0] = __ldg(p0);
     cv[1] = __ldg(p0 + 1);
@@ -398,8 +399,9 @@ __device__ __forceinline__ float composite(const DevScene& s, const uint2 cv[8],
 
 // The adjoint of one composited sample's colour/feature fetch: w_k * (corner weight) *
 // gfeat into the eight corners' gradient entries ([slot][B^3][8], channel 0 unused) with
-// vector atomics. o: the sample's block origin minus one, fl its stencil's lower corner.
-__device__ __forceinline__ void scatter_sample(const DevScene& s, int slot, const float fl[3], const float o[3],
+// vector atomics. o: the sample's block origin minus one, fi its stencil's lower corner
+// (integer voxel coordinates).
+__device__ __forceinline__ void scatter_sample(const DevScene& s, int slot, const int fi[3], const int o[3],
                                                const float f[3], const float g[3], float wk, const float* gfeat,
                                                float* grad_atlas) {
     const int B = s.B, N = s.N;
@@ -409,10 +411,9 @@ __device__ __forceinline__ void scatter_sample(const DevScene& s, int slot, cons
     const int B3 = B * B * B;
     // a stencil inside this block (lower corner at padded coordinate 1 .. B-1 on every
     // axis) has all eight corners in its own slot: no indirection reads
-    const float ex = fl[0] - o[0], ey = fl[1] - o[1], ez = fl[2] - o[2];
-    const float Bm = (float)(B - 1);
-    if (ex >= 1.0f && ex <= Bm && ey >= 1.0f && ey <= Bm && ez >= 1.0f && ez <= Bm) {
-        float* g0 = grad_atlas + ((size_t)slot * B3 + (((int)ez - 1) * B + ((int)ey - 1)) * B + ((int)ex - 1)) * 8;
+    const int ex = fi[0] - o[0], ey = fi[1] - o[1], ez = fi[2] - o[2];
+    if (ex >= 1 && ex <= B - 1 && ey >= 1 && ey <= B - 1 && ez >= 1 && ez <= B - 1) {
+        float* g0 = grad_atlas + ((size_t)slot * B3 + ((ez - 1) * B + (ey - 1)) * B + (ex - 1)) * 8;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             float* gp = g0 + ((((c >> 2) & 1) * B + ((c >> 1) & 1)) * B + (c & 1)) * 8;
@@ -424,9 +425,9 @@ __device__ __forceinline__ void scatter_sample(const DevScene& s, int slot, cons
     } else {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int X = min(max(int_small(fl[0]) + (c & 1), 0), N - 1);
-            const int Y = min(max(int_small(fl[1]) + ((c >> 1) & 1), 0), N - 1);
-            const int Z = min(max(int_small(fl[2]) + ((c >> 2) & 1), 0), N - 1);
+            const int X = min(max(fi[0] + (c & 1), 0), N - 1);
+            const int Y = min(max(fi[1] + ((c >> 1) & 1), 0), N - 1);
+            const int Z = min(max(fi[2] + ((c >> 2) & 1), 0), N - 1);
             const int cs = __ldg(s.ind + (((Z >> s.lgB) * s.G + (Y >> s.lgB)) * s.G + (X >> s.lgB)));
             if (cs < 0) continue;
             const int loc = (((Z & (B - 1)) * B) + (Y & (B - 1))) * B + (X & (B - 1));
@@ -529,9 +530,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
         const uint8_t* vs = vskip + (size_t)slot * s.P3;
         const uint2* pa = s.patlas + (size_t)slot * s.P3;
         // block origin minus one, so that the padded local coordinate is floor(u) - o
-        const float ox = float_small((b[0] << s.lgB) - 1), oy = float_small((b[1] << s.lgB) - 1),
-                    oz = float_small((b[2] << s.lgB) - 1);
-        const float Pf = (float)P;
+        const int o3[3] = {(b[0] << s.lgB) - 1, (b[1] << s.lgB) - 1, (b[2] << s.lgB) - 1};
         float kk = k;
         while (kk < kx) {
             const float tk = lattice_t(r, kk);
@@ -541,20 +540,20 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             // nearest voxel in padded block coordinates, floor(u) - origin + 1: in [1, B] for
             // a sample of this block, or 0 / B+1 where rounding puts u a hair outside the
             // grid -- apron cells that hold the clamped edge voxel's value (the grid clamp
-            // is built into the plane); small integers, exact in binary32. The index clamp
-            // only guards the address.
-            const float lx = floor_small(u[0]) - ox, ly = floor_small(u[1]) - oy, lz = floor_small(u[2]) - oz;
-            const int pidx = min(max(int_small(fmaf(fmaf(lz, Pf, ly), Pf, lx)), 0), s.P3 - 1);
+            // is built into the plane). The index clamp only guards the address.
+            const int lx = floor_int_small(u[0]) - o3[0], ly = floor_int_small(u[1]) - o3[1],
+                      lz = floor_int_small(u[2]) - o3[2];
+            const int pidx = min(max((lz * P + ly) * P + lx, 0), s.P3 - 1);
             // SPEC: the sample's stencil is loaded before the probe's answer when the
             // previous sample was composited (inside a surface the next one usually is
             // too, and one memory latency then serves both), after it otherwise. It pays
             // in latency-bound launches (ray lists, the adjoint); where the launch is
             // issue-bound, lanes that disagree on the guess run the stencil code twice.
-            const float o3[3] = {ox, oy, oz};
             float f[3], g[3], fl[3];
+            int fi[3];
             uint2 cv[8];
             const bool spec = SPEC && (kk == k_spec);
-            if (spec) load_stencil(u, o3, P, s.P3, pa, f, g, fl, cv);
+            if (spec) load_stencil(u, o3, P, s.P3, pa, f, g, fl, fi, cv);
             const int vd = __ldg(vs + pidx);
             if (vd != 0) {
                 // no voxel of this block in the ray's cone within Chebyshev distance vd-1
@@ -570,7 +569,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
             if (k_first && st.active == 0) *k_first = (int)kk;
             st.active++;
             // trilinear stencil on the virtual grid, cell-centred
-            if (!spec) load_stencil(u, o3, P, s.P3, pa, f, g, fl, cv);
+            if (!spec) load_stencil(u, o3, P, s.P3, pa, f, g, fl, fi, cv);
             bool saturated;
             const float wk = composite(s, cv, f, g, st.T, st.tau, saturated);
             if (REC && st.active <= kRecCap) {
@@ -600,7 +599,7 @@ __device__ __forceinline__ void march(const DevScene& s, const Ray& r, MarchStat
 #pragma unroll
                 for (int c = 0; c < 3; ++c) st.rgb_ps[c] = fmaf(wk, cdk[c] + res[c], st.rgb_ps[c]);
             }
-            if (GRAD) scatter_sample(s, slot, fl, o3, f, g, wk, gfeat, grad_atlas);
+            if (GRAD) scatter_sample(s, slot, fi, o3, f, g, wk, gfeat, grad_atlas);
             if (saturated) {
                 steps += kk - k + 1.0f;
                 done = true;
