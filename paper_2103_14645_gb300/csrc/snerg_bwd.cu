@@ -22,8 +22,8 @@ namespace snerg {
 // so rows of neighbouring threads fall in different banks.
 constexpr int kBwdThreads = 128;
 constexpr int kRowX = 0, kRowH1 = 34, kRowH2 = 50, kRowG1 = 66, kRowG2 = 82, kRowGZ = 98, kRow = 101;
-constexpr int kWFloats = 884;
-constexpr int kMaxDevices = 64;     // transposed weights (883) rounded up to a 16-byte multiple
+constexpr int kWFloats = 884;      // transposed weights (883) rounded up to a 16-byte multiple
+constexpr int kMaxDevices = 64;     // devices whose shared-memory opt-in is remembered
 
 size_t backward_smem_bytes() { return (size_t)(kWFloats + kBwdThreads * kRow) * sizeof(float); }
 
