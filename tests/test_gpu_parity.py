@@ -91,15 +91,29 @@ def test_forward_parity_paper_scale_view():
 @pytest.mark.parametrize("name", ["gauss64", "shell1024"])
 def test_rays_path_equals_image_path(name):
     """Every pixel of the views as one ray list renders what the image launch renders, bit
-    for bit: 4,096 rays (one wave: the ray-list build limited to 4 CTAs per SM) and the
-    640,000 of the 800x800 view (the 8-CTA build)."""
+    for bit (colours, counts, composites, visited voxels): 4,096 rays (one wave: the
+    ray-list build limited to 4 CTAs per SM) and the 640,000 of the 800x800 view (the 8-CTA
+    build), with device weights and with weights as kernel parameters."""
     sc = scene(name)
-    g, r = gpu_render(sc)
-    pix = synth.all_pixels(sc.cameras)
+    g, r = gpu_render(sc, aux=True, counts=True, trace_cap=8)
+    pix = torch.from_numpy(synth.all_pixels(sc.cameras)).to(DEV)
     w = torch.from_numpy(sc.mlp).to(DEV)
-    rr = r.render_rays(sc.cameras, torch.from_numpy(pix).to(DEV), w).cpu().numpy()
+    rr = r.render_rays(sc.cameras, pix, w).cpu().numpy()
     r.check_status()
     np.testing.assert_array_equal(rr, g["rgb"])
+    # the debug build of each size (counts, composites, the first visited voxels), device
+    # weights and weights as kernel parameters
+    r.set_mlp(sc.mlp)
+    for mlp in (w, None):
+        d = r.render_rays(sc.cameras, pix, mlp, aux=True, counts=True, trace_cap=8)
+        r.check_status()
+        if mlp is None:      # the parameter-weight MLP rounds its sums in another order
+            np.testing.assert_allclose(d["rgb"].cpu().numpy(), g["rgb"], rtol=0, atol=1e-6)
+        else:
+            np.testing.assert_array_equal(d["rgb"].cpu().numpy(), g["rgb"])
+        np.testing.assert_array_equal(d["counts"].cpu().numpy(), g["counts"])
+        np.testing.assert_array_equal(d["aux"].cpu().numpy(), g["aux"])
+        np.testing.assert_array_equal(d["trace"].cpu().numpy(), g["trace"])
 
 
 @pytest.mark.parametrize("tile", [None, (8, 4), (4, 8), (16, 2), (32, 1), (8, 16)])
