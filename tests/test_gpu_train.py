@@ -228,6 +228,30 @@ def test_train_rays_matches_oracle_and_the_separate_launches(flags):
     assert (gm - gm2).abs().max().item() <= 1e-5 * max(gm2.abs().max().item(), 1e-30)
 
 
+def test_train_rays_at_the_benchmarked_batch():
+    """The one-launch training step in the launch configuration the bench times (the 512^3
+    grid, its 65,536 listed rays over 8 views and their targets): colours, loss, atlas and
+    MLP gradients against the FP64 oracle."""
+    sc = synth.make_scene("bwd512")
+    pix_np, target = sc.extra["pix"], sc.extra["target"]
+    r = renderer.Renderer.from_scene(sc, DEV)
+    pix = torch.from_numpy(pix_np).to(DEV)
+    w = torch.from_numpy(sc.mlp).to(DEV)
+    ga = torch.zeros(sc.atlas.shape, dtype=torch.float32, device=DEV)
+    gm = torch.zeros(883, dtype=torch.float32, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+    rgb = torch.empty((pix_np.shape[0], 3), dtype=torch.float32, device=DEV)
+    r.train_rays(sc.cameras, pix, w, torch.from_numpy(target).to(DEV), ga, gm, loss=loss, out=rgb)
+    r.check_status()
+    o = oracle.render_rays(sc, pix_np)
+    d = o["rgb"] - target
+    ra, rm = oracle.backward_rays(sc, pix_np, 2.0 * d)
+    assert np.abs(rgb.cpu().numpy() - o["rgb"]).max() <= 1e-4
+    np.testing.assert_allclose(float(loss.item()), float((d * d).sum()), rtol=1e-4)
+    assert np.abs(ga.cpu().numpy() - ra).max() <= 1e-4 * np.abs(ra).max()
+    assert np.abs(gm.cpu().numpy() - rm).max() <= 1e-4 * np.abs(rm).max()
+
+
 def test_finetuner_large_batch_takes_the_separate_launches():
     """A batch larger than the fused limit (8 waves of the adjoint kernel; forced here)
     goes through render_rays -> l2_loss -> backward; one step gives the same loss and
