@@ -205,6 +205,9 @@ def run_reference(args, ws, rank):
         return
     import oracle
     from paper_2103_14645_gb300 import synth
+    # rank 0 runs alone (the other ranks have returned): every host core this process may
+    # use, whatever thread count a launcher set for per-rank work
+    oracle.set_threads(len(os.sched_getaffinity(0)))
     sc = synth.make_scene("shell1024")
     pix_all = synth.all_pixels(sc.cameras)
     # a bounded sample per step: a seeded quarter of the view's rays
